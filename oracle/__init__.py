@@ -1,0 +1,183 @@
+"""ctypes wrapper of the FP64 CPU oracle (``oracle/tlb_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use it; the CUDA library never does.  It
+takes plain numpy arrays and shares no code with the GPU path.
+
+State layout: ``state[27, ny, nx]`` float64, planes 0-8 component 1, 9-17
+component 2, 18-26 thermal, holding the pre-collision populations S_t.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIBS = {}
+
+
+class OrcParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int),
+        ("ny", ctypes.c_int),
+        ("periodic_y", ctypes.c_int),
+        ("_pad", ctypes.c_int),
+        ("tau", ctypes.c_double),
+        ("tau_g", ctypes.c_double),
+        ("rho0", ctypes.c_double),
+        ("G12", ctypes.c_double),
+        ("Ga", ctypes.c_double * 2),
+        ("Gr", ctypes.c_double * 2),
+        ("rho_wall", ctypes.c_double * 2),
+        ("T_down", ctypes.c_double),
+        ("T_up", ctypes.c_double),
+        ("alpha_g", ctypes.c_double),
+        ("body_fx", ctypes.c_double),
+    ]
+
+
+_PARAM_KEYS = ("nx", "ny", "periodic_y", "tau", "tau_g", "rho0", "G12", "Ga", "Gr", "rho_wall",
+               "T_down", "T_up", "alpha_g", "body_fx")
+
+
+def lib(omp=False):
+    key = bool(omp)
+    if key not in _LIBS:
+        _build.build()
+        L = ctypes.CDLL(_build.lib_path(omp))
+        dp = ctypes.POINTER(ctypes.c_double)
+        u8 = ctypes.c_void_p
+        P = ctypes.POINTER(OrcParams)
+        L.orc_tables.argtypes = [ctypes.POINTER(ctypes.c_int), dp, dp]
+        L.orc_solid_map.argtypes = [P, u8, u8]
+        L.orc_init.argtypes = [P, u8, dp, dp, dp, dp]
+        L.orc_forces.argtypes = [P, u8, dp, dp, dp, dp]
+        L.orc_step.argtypes = [P, u8, dp, dp]
+        L.orc_run.argtypes = [P, u8, dp, dp, ctypes.c_long]
+        L.orc_fields.argtypes = [P, u8, dp, dp, dp, dp, dp, dp]
+        L.orc_observables.argtypes = [P, u8, dp, dp]
+        for f in ("orc_solid_map", "orc_init", "orc_forces", "orc_step", "orc_run", "orc_fields",
+                  "orc_observables"):
+            getattr(L, f).restype = ctypes.c_int
+        _LIBS[key] = L
+    return _LIBS[key]
+
+
+def make_params(p):
+    """Build the C struct from a dict with the keys of ``_PARAM_KEYS`` (missing ones default to 0)."""
+    s = OrcParams()
+    for k in _PARAM_KEYS:
+        if k not in p:
+            continue
+        v = p[k]
+        if k in ("Ga", "Gr", "rho_wall"):
+            getattr(s, k)[0] = float(v[0])
+            getattr(s, k)[1] = float(v[1])
+        elif k in ("nx", "ny", "periodic_y"):
+            setattr(s, k, int(v))
+        else:
+            setattr(s, k, float(v))
+    return s
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _mask(mask):
+    if mask is None:
+        return None, None
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    return m, m.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed (rc={rc})")
+
+
+def tables():
+    c = (ctypes.c_int * 50)()
+    w = np.zeros(9)
+    p = np.zeros(25)
+    lib().orc_tables(c, _dp(w), _dp(p))
+    return np.array(list(c), dtype=np.int64).reshape(25, 2), w, p
+
+
+class Oracle:
+    """One lattice: parameters, obstacle mask and the FP64 state S_t."""
+
+    def __init__(self, params, rho1, rho2, T0, mask=None, omp=False):
+        self.p = dict(params)
+        self.cp = make_params(self.p)
+        self.nx, self.ny = int(self.p["nx"]), int(self.p["ny"])
+        self._mask_arr, self._mask_ptr = _mask(mask)
+        self.L = lib(omp)
+        shape = (self.ny, self.nx)
+        r1 = np.ascontiguousarray(np.broadcast_to(rho1, shape), dtype=np.float64)
+        r2 = np.ascontiguousarray(np.broadcast_to(rho2, shape), dtype=np.float64)
+        t0 = np.ascontiguousarray(np.broadcast_to(T0, shape), dtype=np.float64)
+        self.state = np.zeros((27, self.ny, self.nx))
+        self.work = np.zeros_like(self.state)
+        _check(self.L.orc_init(ctypes.byref(self.cp), self._mask_ptr, _dp(r1), _dp(r2), _dp(t0), _dp(self.state)),
+               "init")
+        self.step_count = 0
+
+    @classmethod
+    def from_state(cls, params, state, mask=None, omp=False):
+        o = cls.__new__(cls)
+        o.p = dict(params)
+        o.cp = make_params(o.p)
+        o.nx, o.ny = int(o.p["nx"]), int(o.p["ny"])
+        o._mask_arr, o._mask_ptr = _mask(mask)
+        o.L = lib(omp)
+        o.state = np.ascontiguousarray(state, dtype=np.float64).copy()
+        o.work = np.zeros_like(o.state)
+        o.step_count = 0
+        return o
+
+    def step(self, n=1):
+        _check(self.L.orc_run(ctypes.byref(self.cp), self._mask_ptr, _dp(self.state), _dp(self.work), int(n)), "run")
+        self.step_count += n
+        return self
+
+    def fields(self):
+        N = (self.ny, self.nx)
+        r1, r2, T, ux, uy = (np.zeros(N) for _ in range(5))
+        _check(self.L.orc_fields(ctypes.byref(self.cp), self._mask_ptr, _dp(self.state), _dp(r1), _dp(r2), _dp(T),
+                                 _dp(ux), _dp(uy)), "fields")
+        return {"rho1": r1, "rho2": r2, "T": T, "ux": ux, "uy": uy}
+
+    def observables(self):
+        out = np.zeros(8)
+        _check(self.L.orc_observables(ctypes.byref(self.cp), self._mask_ptr, _dp(self.state), _dp(out)),
+               "observables")
+        return {"mass": out[0:2].copy(), "mom": out[2:4].copy(), "Nu": out[4], "E": out[5], "n_bad": int(out[6]),
+                "n_fluid": int(out[7])}
+
+    def solid(self):
+        s = np.zeros((self.ny, self.nx), dtype=np.uint8)
+        _check(self.L.orc_solid_map(ctypes.byref(self.cp), self._mask_ptr, s.ctypes.data_as(ctypes.c_void_p)),
+               "solid_map")
+        return s
+
+
+def forces(params, rho1, rho2, T, mask=None):
+    """F[l, xy, ny, nx] of Eqs. (FAB)+(FintAttrattive)+(FintRepulsive)+(alphaG) for given fields."""
+    cp = make_params(params)
+    ny, nx = int(params["ny"]), int(params["nx"])
+    r1 = np.ascontiguousarray(rho1, dtype=np.float64)
+    r2 = np.ascontiguousarray(rho2, dtype=np.float64)
+    t = np.ascontiguousarray(np.broadcast_to(T, (ny, nx)), dtype=np.float64)
+    F = np.zeros((2, 2, ny, nx))
+    m, mp = _mask(mask)
+    _check(lib().orc_forces(ctypes.byref(cp), mp, _dp(r1), _dp(r2), _dp(t), _dp(F)), "forces")
+    return F
+
+
+def available_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
