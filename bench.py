@@ -1,0 +1,345 @@
+"""Benchmark of the fused thermal emulsion lattice Boltzmann step on GB300.
+
+Workload: the 1024 x 512 concentrated emulsion (350 droplets, phi = 0.8,
+Ra = 3.6e4), synthetic and seeded.  One bench step = one lattice update of
+the whole lattice by the fused kernel.  Headline: the FP32-shifted storage
+form; the FP64 form is measured on the same workload and reported beside it.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+on the launching stream; before every timed step a 512 MiB buffer is written
+(L2 flush), because the FP32 working set (113 MB) fits in the 135 MB L2.
+MLUPS = nx * ny * K / sum(step times) / 1e6 (all lattice nodes).
+
+``--impl reference`` times the FP64 CPU oracle (OpenMP build, all host
+cores) on the same workload and metric, each step a full lattice update.
+
+Multi-GPU: the step does not shard in this build; under torchrun each rank
+runs an independent replica (no data-path collective) and rank 0 reports
+the aggregate over ranks with the max-over-ranks time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline: FP64 vs FP32-shifted vs batched; adjoint/forward cost"
+FLUSH_BYTES = 512 << 20
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return PEAKS_FALLBACK["hbm_gbs"], "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2109_12565_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fn.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profile_counters():
+    """Per-launch DRAM traffic of the step kernels from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            d = json.load(fh)
+    except Exception:
+        return {}
+    if d.get("kernel_sources_sha256_16") != _kernel_hash():
+        return {}
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap,utilization.gpu")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(s[0]) for s in self.samples if num(s[0]) is not None]
+        util = [num(s[7]) or 0.0 for s in self.samples]
+        loaded = [num(s[0]) for s in self.samples if (num(s[7]) or 0.0) > 50 and num(s[0]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            for k, n in enumerate(names):
+                if s[3 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(loaded or sm), "sm_max_mhz": num(self.samples[0][1]),
+                "reasons": sorted(reasons), "samples": len(self.samples),
+                "samples_under_load": len(loaded), "max_util": max(util) if util else None}
+
+
+def time_form(w, precision, steps, warmup, flush):
+    """Per-step CUDA-event timing of the fused step on the Lattice's stream, L2 flushed before each step."""
+    import torch
+
+    from paper_2109_12565_gb300 import lb
+
+    g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, mask=w.mask, precision=precision)
+    s = g.stream
+    with torch.cuda.stream(s):
+        for _ in range(warmup):
+            flush.fill_(1)
+            g.step(1)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(s)
+            g.step(1)
+            ev[k][1].record(s)
+        torch.cuda.synchronize()
+    times = [a.elapsed_time(b) for a, b in ev]
+    obs = g.observables()
+    g.close()
+    return {"ms_total": sum(times), "ms_per_step": sum(times) / steps, "ms_min": min(times),
+            "ms_median": statistics.median(times), "obs": obs}
+
+
+def time_e2e(w, precision, steps, obs_every=500):
+    """End to end through the C ABI: lb_init from pinned host fields, `steps` steps (graph replays),
+    observables every `obs_every` steps and at the end, fields back to pinned host memory."""
+    import numpy as np
+    import torch
+
+    from paper_2109_12565_gb300 import lb
+
+    N = w.params["nx"] * w.params["ny"]
+    host_in = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory() for a in
+               (w.rho1, w.rho2, w.T0)]
+    arrays = [t.numpy() for t in host_in]
+    out = torch.empty((5, w.params["ny"], w.params["nx"]), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = lb.Lattice(w.params, arrays[0], arrays[1], arrays[2], mask=w.mask, precision=precision)
+    done, n_obs = 0, 0
+    while done < steps:
+        n = min(obs_every, steps - done)
+        g.step(n)
+        done += n
+        g.observables()
+        n_obs += 1
+    o = out.numpy()
+    import ctypes
+    dp = [o[k].ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for k in range(5)]
+    rc = lb.lib().lb_get_fields(g._h, *dp)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    assert rc == 0
+    g.close()
+    h2d = 3 * N * 8 + (N if w.mask is not None else 0)
+    d2h = n_obs * 16 * 8 + 5 * N * 8
+    return {"value": N * steps / (t1 - t0) / 1e6, "unit": "MLUPS", "seconds": t1 - t0,
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps, "steps": steps,
+            "observables_every": obs_every}
+
+
+def cpu_baseline(w, seconds=12.0, min_steps=2):
+    """The FP64 oracle as it stands (OpenMP build, all host cores) on the same workload."""
+    import oracle as O
+
+    cores = O.available_cores()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    o = O.Oracle(w.params, w.rho1, w.rho2, w.T0, mask=w.mask, omp=True)
+    o.step(1)
+    n, t0 = 0, time.perf_counter()
+    while n < min_steps or time.perf_counter() - t0 < seconds:
+        o.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    N = w.params["nx"] * w.params["ny"]
+    return {"value": N * n / dt / 1e6, "unit": "MLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle", "sample": f"{n} full steps of the {w.name} lattice after 1 untimed step "
+                                        f"({dt:.1f} s, FP64 C oracle, OpenMP over rows)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2109_12565_gb300 import inputs as I
+    import oracle as O
+
+    w = I.emulsion_1024x512()
+    cores = O.available_cores()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    o = O.Oracle(w.params, w.rho1, w.rho2, w.T0, omp=True)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    N = w.params["nx"] * w.params["ny"]
+    v = N * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "nx": 1024, "ny": 512, "n_drops": 350,
+                                             "phi": 0.8, "Ra": 3.6e4},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]),
+                             "kind": "oracle",
+                             "sample": f"{args.steps} full steps of {w.name} after {args.warmup} warm-up steps"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2000)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2109_12565_gb300 import build as B
+    from paper_2109_12565_gb300 import inputs as I
+    from paper_2109_12565_gb300 import lb
+
+    B.build()
+    w = I.emulsion_1024x512()
+    N = w.params["nx"] * w.params["ny"]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        r32 = time_form(w, lb.LB_FP32_SHIFTED, args.steps, args.warmup, flush)
+        r64 = time_form(w, lb.LB_FP64, max(3, args.steps // 4), args.warmup, flush)
+    torch.cuda.synchronize()
+    t32, t64 = r32["ms_total"], r64["ms_total"]
+    if dist:
+        t = torch.tensor([t32, t64], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t32, t64 = float(t[0]), float(t[1])
+    steps64 = max(3, args.steps // 4)
+    mlups32 = world * N * args.steps / (t32 * 1e3)
+    mlups64 = world * N * steps64 / (t64 * 1e3)
+    e2e = time_e2e(w, lb.LB_FP32_SHIFTED, args.e2e_steps)
+    if dist:
+        t = torch.tensor([e2e["seconds"]], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e["value"] = world * N * args.e2e_steps / float(t[0]) / 1e6
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+    peak, peak_kind = _peaks()
+    prof = _profile_counters()
+    bytes32, bytes64 = 216.0 * N, 432.0 * N  # 27 populations read + written per node
+    ach32 = bytes32 / (r32["ms_per_step"] * 1e-3) / 1e9
+    ach64 = bytes64 / (r64["ms_per_step"] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s", "frac": ach32 / peak,
+            "traffic": prof.get("fp32_step_dram_bytes_per_launch"), "peak_source": peak_kind,
+            "kernel": "lb_step_kernel<float, shifted> (fused step)", "algorithmic_bytes_per_launch": bytes32}
+    forms = {
+        "fp32_shifted": {"MLUPS": mlups32, "ms_per_step": r32["ms_per_step"], "hbm_frac": ach32 / peak,
+                         "GBps": ach32, "Nu": r32["obs"]["Nu"]},
+        "fp64": {"MLUPS": mlups64, "ms_per_step": r64["ms_per_step"], "hbm_frac": ach64 / peak, "GBps": ach64,
+                 "bound": "alu (FP64 pipe)", "traffic": prof.get("fp64_step_dram_bytes_per_launch"),
+                 "Nu": r64["obs"]["Nu"]},
+        "fp32_over_fp64": mlups32 / mlups64,
+    }
+    dp = prof.get("fp64_dp_flops_per_node")
+    if dp:
+        forms["fp64"]["dp_tflops"] = dp * N / (r64["ms_per_step"] * 1e-3) / 1e12
+        forms["fp64"]["alu_frac_of_nominal"] = forms["fp64"]["dp_tflops"] / FP64_NOMINAL_TFLOPS
+    line = {
+        "metric": METRIC, "value": mlups32, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "nx": 1024, "ny": 512, "n_drops": 350, "phi": 0.8, "Ra": 3.6e4,
+                   "form": "fp32_shifted", "l2": "flushed before every timed step (512 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roof,
+        "forms": forms,
+        "e2e": e2e,
+        "gpu_launches": args.steps + steps64,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, seconds=args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

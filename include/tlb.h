@@ -1,0 +1,147 @@
+/*
+ * tlb.h - C ABI of the GB300 (sm_103a) thermal two-component lattice
+ * Boltzmann library: the per-time-step update of a 2D emulsion model
+ * (TLBfind, arXiv 2109.12565, Sec. 2.1-2.3) on one GPU.
+ *
+ * Model (Sec. 2.1-2.3): two D2Q9 fluid components f_{l,i} (l = 1, 2) and
+ * one D2Q9 thermal population g_i.  Per step, at every fluid node:
+ *   rho_l = sum_i f_{l,i},  u = sum_{l,i} c_i f_{l,i} / (rho_1 + rho_2),
+ *   T = sum_i g_i                                   (Sec. 2.1 moments, Sec. 2.3)
+ *   F_l = F^x_l + F^a_l + F^r_l + F^ext_l            (Eqs. FAB, FintAttrattive,
+ *         F^ext_l = rho_l alpha_g T e_y               FintRepulsive, alphaG)
+ *   u_l = u + tau F_l / rho_l                        (Eq. shift)
+ *   u^(H) = u + F / (2 rho),  F = F_1 + F_2          (text after Eq. NS)
+ *   f*_{l,i} = f - (f - f^eq(rho_l, u_l)) / tau      (Eq. BGK)
+ *   g*_i = g - (g - g^eq(T, u^(H))) / tau_g          (Eq. LBMg, Eq. Teq)
+ *   f(x + c_i, t + 1) = f*(x, t)                     (Eq. LBM, streaming)
+ * with psi~ = rho/rho0 in F^x and psi = rho0 (1 - exp(-rho/rho0)) in F^a, F^r.
+ * A link that ends on a solid node bounces back half-way (Sec. 2.2, zero wall
+ * velocity); the thermal population is anti-bounced to hold the wall at its
+ * temperature: g_{-i}(x, t + 1) = -g*_i(x, t) + 2 w_i T_w.  Every solid or
+ * out-of-domain position reached by a force stencil carries the wall
+ * densities rho_wall (Sec. 2.2.1).
+ *
+ * Grid: nx * ny nodes, x fastest, x periodic.  periodic_y = 0: rows y = 0 and
+ * y = ny - 1 are solid walls (hot bottom at T_down, cold top at T_up);
+ * periodic_y = 1: fully periodic, no walls, no obstacle mask allowed.
+ * An optional obstacle mask (host, nx * ny bytes, nonzero = solid) adds
+ * solid nodes (rough-wall posts); a solid node in the lower half of the
+ * lattice is at T_down, in the upper half at T_up.
+ *
+ * Memory: the caller owns the device workspace (size from
+ * lb_workspace_size, 256-byte aligned) and the CUDA stream; the library owns
+ * only its host-side handle and its CUDA graph objects.  Host arrays passed
+ * to the library are read or written before the call returns.  Every call
+ * returns one of the LB_* codes below; lb_last_error gives the text.
+ * Nothing throws across this interface.
+ */
+#ifndef TLB_H
+#define TLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LB_OK 0
+#define LB_EINVAL (-1)      /* invalid argument or parameter */
+#define LB_ENOSPACE (-2)    /* workspace too small or misaligned */
+#define LB_ECUDA (-3)       /* a CUDA runtime call failed */
+#define LB_ETIMEOUT (-4)    /* a bounded device-side wait ran out */
+#define LB_EUNSTABLE (-5)   /* non-finite or non-positive density detected */
+
+/* Storage precision of the populations. */
+#define LB_FP64 0           /* FP64 populations, FP64 arithmetic */
+#define LB_FP32_SHIFTED 1   /* FP32 deviations f - w_i rho_bar_l, g - w_i T_bar; FP32 arithmetic;
+                               FP64 shift constants and FP64 reductions */
+
+typedef struct lb_params {
+  int nx, ny;          /* lattice size including wall rows */
+  int periodic_y;      /* 0: solid rows y = 0, ny-1; 1: periodic in y */
+  int precision;       /* LB_FP64 or LB_FP32_SHIFTED */
+  double tau;          /* fluid relaxation time (> 1/2), Eq. BGK */
+  double tau_g;        /* thermal relaxation time (> 1/2), Eq. LBMg */
+  double rho0;         /* reference density of psi~ and psi (> 0) */
+  double G12;          /* inter-component coupling, Eq. FAB */
+  double Ga[2];        /* G^a_11, G^a_22 (attraction, < 0 in the paper), Eq. FintAttrattive */
+  double Gr[2];        /* G^r_11, G^r_22 (repulsion, > 0), Eq. FintRepulsive */
+  double rho_wall[2];  /* wall densities: component 1 (rho_w,max), component 2 (rho_w,min) */
+  double T_down, T_up; /* bottom / top wall temperature */
+  double alpha_g;      /* buoyancy alpha * g, Eq. alphaG */
+  double body_fx;      /* constant x acceleration on both components (0 in the paper's runs) */
+  double shift_rho[2]; /* LB_FP32_SHIFTED: rho_bar_l; NaN = mean initial density of the fluid nodes */
+  double shift_T;      /* LB_FP32_SHIFTED: T_bar; NaN = (T_down + T_up) / 2 */
+} lb_params;
+
+/* Observables of the current state S_t (pre-collision populations at step t). */
+typedef struct lb_obs {
+  double mass[2];      /* sum over fluid nodes of rho_l */
+  double mom[2];       /* sum over fluid nodes of rho u^(H) */
+  double Nu;           /* Nusselt number, Eq. NuTime: (<u^(H)_y T> - kappa <dT/dy>) / (kappa dT / H),
+                          <.> over fluid nodes, dT/dy central with mirror 2 T_w - T at solid
+                          neighbours, H = ny - 2, dT = T_down - T_up; 0 if periodic_y or dT = 0 */
+  double E;            /* <|u^(H)|^2> over fluid nodes */
+  long long step;      /* number of steps taken since lb_init / lb_set_state */
+  long long n_fluid;   /* number of fluid nodes */
+  long long n_bad;     /* fluid nodes with a non-finite or non-positive density or non-finite T */
+  int status;          /* LB_OK, or LB_EUNSTABLE when n_bad > 0 */
+  int _pad;
+} lb_obs;
+
+typedef struct lb_handle lb_handle;
+
+/* Bytes of device workspace lb_init needs for these parameters; has_mask != 0 when an obstacle
+ * mask will be passed.  Returns LB_EINVAL on invalid parameters. */
+int lb_workspace_size(const lb_params* p, int has_mask, size_t* bytes);
+
+/* Create a lattice on the current CUDA device.  rho1, rho2, T0: host arrays of nx*ny doubles (x
+ * fastest) with the initial densities and temperature; the initial populations are the rest
+ * equilibria f_{l,i} = w_i rho_l, g_i = w_i T0 at fluid nodes.  mask: host nx*ny bytes or NULL.
+ * d_workspace: device memory of ws_bytes >= lb_workspace_size, 256-byte aligned, owned by the
+ * caller and not touched by anyone else while the handle lives.  stream: cudaStream_t or NULL for
+ * the legacy default stream; every later call is ordered on it.  Blocks until the state is on the
+ * device.  Errors: LB_EINVAL (bad parameters, tau <= 1/2, non-positive initial density, mask with
+ * periodic_y), LB_ENOSPACE, LB_ECUDA. */
+int lb_init(lb_handle** h, const lb_params* p, const uint8_t* mask, const double* rho1, const double* rho2,
+            const double* T0, void* d_workspace, size_t ws_bytes, void* stream);
+
+/* Advance n >= 0 time steps.  Asynchronous on the handle's stream (CUDA-graph replay of one fused
+ * kernel per step). */
+int lb_step(lb_handle* h, int n);
+
+/* Observables of the current state.  Synchronises the stream; returns LB_EUNSTABLE (with *out
+ * filled) when any fluid node has a non-finite or non-positive density. */
+int lb_observables(lb_handle* h, lb_obs* out);
+
+/* Hydrodynamic fields of the current state into host arrays of nx*ny doubles (any may be NULL):
+ * rho1, rho2, T, u^(H)_x, u^(H)_y.  Solid nodes report rho_wall, the wall temperature and zero
+ * velocity.  Synchronous. */
+int lb_get_fields(lb_handle* h, double* rho1, double* rho2, double* T, double* ux, double* uy);
+
+/* Copy the populations of S_t to / from host memory as 27 planes of nx*ny doubles (planes 0-8
+ * f_{1,i}, 9-17 f_{2,i}, 18-26 g_i, D2Q9 order (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1)
+ * (-1,-1) (1,-1)); solid nodes read as 0 and are ignored on write.  In LB_FP32_SHIFTED the
+ * stored deviations are converted to full populations.  bytes must equal 27*nx*ny*8.
+ * lb_set_state resets the step counter.  Synchronous. */
+int lb_get_state(lb_handle* h, double* host, size_t bytes);
+int lb_set_state(lb_handle* h, const double* host, size_t bytes);
+
+/* Wait for all work of the handle and report any asynchronous CUDA error. */
+int lb_sync(lb_handle* h);
+
+/* Release the handle and its graphs (not the caller's workspace or stream). */
+void lb_destroy(lb_handle* h);
+
+/* Text of the last error on this handle, or of the last failed lb_init / lb_workspace_size of
+ * this thread when h is NULL.  Never NULL. */
+const char* lb_last_error(const lb_handle* h);
+
+/* Library version string. */
+const char* lb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,63 @@
+// Internal launch configuration of the CUDA library (host and device view).
+// Every constant the fused step needs is precomputed on the host in FP64 and
+// passed by value; the FP32 kernels round them once.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tlb {
+
+enum Mode : int { MODE_STEP = 0, MODE_OBS = 1, MODE_FIELDS = 2 };
+
+// Number of doubles each block writes to the partial-sum buffer in MODE_OBS.
+constexpr int kObsSlots = 10;
+// Final observable vector written by the reduction kernel.
+constexpr int kObsOut = 16;
+
+struct StepCfg {
+  int nx, ny;           // lattice
+  int pitch;            // elements per stored row (>= nx, rows 128-byte aligned)
+  int periodic_y;
+  long long plane;      // elements per population plane = pitch * ny
+  const uint8_t* mask;  // device obstacle mask (nx * ny, unpadded) or nullptr
+  double tau;           // tau (velocity shift, Eq. shift)
+  double inv_tau, inv_tau_g;
+  double rho0, inv_rho0;
+  double gx;            // G12 / rho0^2: Eq. FAB written on rho instead of psi~ = rho / rho0
+  // Self-interaction weights per shell, G^a w_i + G^r p_i (Eqs. FintAttrattive + FintRepulsive),
+  // for |c|^2 = 1, 2 and twice the weight for |c|^2 = 4, 8 (those links have |c_x| or |c_y| = 2).
+  double a1[2], a2[2], a4x2[2], a5[2], a8x2[2];
+  double rho_w[2], psi_w[2];  // wall densities and their exp pseudo-potentials
+  double T_down, T_up;
+  double alpha_g, body_fx;
+  double rho_bar[2], T_bar;   // storage shifts (0 in FP64)
+  double kappa;               // (tau_g - 1/2) / 3, Eq. K
+  double H;                   // wall-to-wall height ny - 2
+};
+
+// Tile shapes (nodes per CTA in x and y; threads per CTA = TX * BY).
+template <class S> struct Tile;
+template <> struct Tile<double> { static constexpr int TX = 32, TY = 16, BY = 8; };
+template <> struct Tile<float> { static constexpr int TX = 64, TY = 16, BY = 4; };
+
+inline dim3 grid_for(int nx, int ny, int tx, int ty) {
+  return dim3((unsigned)((nx + tx - 1) / tx), (unsigned)((ny + ty - 1) / ty), 1u);
+}
+
+// ---- launchers (one translation unit per storage precision) ----
+// mode MODE_STEP: fin -> fout;  MODE_OBS: aux = per-block partials (kObsSlots doubles each);
+// MODE_FIELDS: aux = 5 planes of nx*ny doubles (rho1, rho2, T, ux, uy).
+cudaError_t launch_f64(int mode, const StepCfg& c, const void* fin, void* fout, double* aux, cudaStream_t s);
+cudaError_t launch_f32(int mode, const StepCfg& c, const void* fin, void* fout, double* aux, cudaStream_t s);
+// Initial rest equilibria from 3 planes (rho1, rho2, T) of nx*ny doubles.
+cudaError_t init_f64(const StepCfg& c, const double* fields, void* buf, cudaStream_t s);
+cudaError_t init_f32(const StepCfg& c, const double* fields, void* buf, cudaStream_t s);
+// One population plane k to / from nx*ny doubles (full populations; solid nodes 0 / ignored).
+cudaError_t plane_get_f64(const StepCfg& c, int k, const void* buf, double* out, cudaStream_t s);
+cudaError_t plane_get_f32(const StepCfg& c, int k, const void* buf, double* out, cudaStream_t s);
+cudaError_t plane_put_f64(const StepCfg& c, int k, const double* in, void* buf, cudaStream_t s);
+cudaError_t plane_put_f32(const StepCfg& c, int k, const double* in, void* buf, cudaStream_t s);
+// Deterministic final reduction of n_blocks partials into kObsOut doubles.
+cudaError_t obs_finalize(const StepCfg& c, const double* partials, int n_blocks, double* out, cudaStream_t s);
+
+}  // namespace tlb

@@ -1,0 +1,28 @@
+// FP32-shifted instantiation of the fused step: populations stored as FP32
+// deviations from the rest equilibria of the shift densities (f - w_i rho_bar_l,
+// g - w_i T_bar), FP32 arithmetic; the shift constants stay FP64 on the host
+// and in the reductions.
+#include "lb_kernels.cuh"
+
+namespace tlb {
+
+cudaError_t launch_f32(int mode, const StepCfg& c, const void* fin, void* fout, double* aux, cudaStream_t s) {
+  return launch_impl<float, true>(mode, c, fin, fout, aux, s);
+}
+
+cudaError_t init_f32(const StepCfg& c, const double* fields, void* buf, cudaStream_t s) {
+  lb_init_kernel<float, true><<<rows_grid(c), 128, 0, s>>>(fields, static_cast<float*>(buf), c);
+  return cudaGetLastError();
+}
+
+cudaError_t plane_get_f32(const StepCfg& c, int k, const void* buf, double* out, cudaStream_t s) {
+  lb_plane_get_kernel<float, true><<<rows_grid(c), 128, 0, s>>>(k, static_cast<const float*>(buf), out, c);
+  return cudaGetLastError();
+}
+
+cudaError_t plane_put_f32(const StepCfg& c, int k, const double* in, void* buf, cudaStream_t s) {
+  lb_plane_put_kernel<float, true><<<rows_grid(c), 128, 0, s>>>(k, in, static_cast<float*>(buf), c);
+  return cudaGetLastError();
+}
+
+}  // namespace tlb

@@ -1,0 +1,183 @@
+"""Thin ctypes binding of the C ABI in ``include/tlb.h`` (argument marshalling only).
+
+Device memory comes from PyTorch (one uint8 workspace tensor per lattice) and
+the CUDA stream is PyTorch's current stream; every step of the method runs
+in the library's kernels.  The binding raises if the CUDA library has not
+been built: there is no CPU fallback.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtlbgb300.so")
+
+LB_OK, LB_EINVAL, LB_ENOSPACE, LB_ECUDA, LB_ETIMEOUT, LB_EUNSTABLE = 0, -1, -2, -3, -4, -5
+LB_FP64, LB_FP32_SHIFTED = 0, 1
+_NAMES = {0: "LB_OK", -1: "LB_EINVAL", -2: "LB_ENOSPACE", -3: "LB_ECUDA", -4: "LB_ETIMEOUT", -5: "LB_EUNSTABLE"}
+
+# every symbol include/tlb.h declares
+EXPORTS = ("lb_workspace_size", "lb_init", "lb_step", "lb_observables", "lb_get_fields", "lb_get_state",
+           "lb_set_state", "lb_sync", "lb_destroy", "lb_last_error", "lb_version")
+
+
+class LbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class LbParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("periodic_y", ctypes.c_int), ("precision", ctypes.c_int),
+        ("tau", ctypes.c_double), ("tau_g", ctypes.c_double), ("rho0", ctypes.c_double), ("G12", ctypes.c_double),
+        ("Ga", ctypes.c_double * 2), ("Gr", ctypes.c_double * 2), ("rho_wall", ctypes.c_double * 2),
+        ("T_down", ctypes.c_double), ("T_up", ctypes.c_double), ("alpha_g", ctypes.c_double),
+        ("body_fx", ctypes.c_double), ("shift_rho", ctypes.c_double * 2), ("shift_T", ctypes.c_double),
+    ]
+
+
+class LbObs(ctypes.Structure):
+    _fields_ = [
+        ("mass", ctypes.c_double * 2), ("mom", ctypes.c_double * 2), ("Nu", ctypes.c_double), ("E", ctypes.c_double),
+        ("step", ctypes.c_longlong), ("n_fluid", ctypes.c_longlong), ("n_bad", ctypes.c_longlong),
+        ("status", ctypes.c_int), ("_pad", ctypes.c_int),
+    ]
+
+
+_LIB = None
+
+
+def lib():
+    """Load the library (raises if it was not built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built ({LIB_PATH} missing): run paper_2109_12565_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, dp, i, sz = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_size_t
+        P = ctypes.POINTER(LbParams)
+        L.lb_workspace_size.argtypes = [P, i, ctypes.POINTER(sz)]
+        L.lb_init.argtypes = [ctypes.POINTER(vp), P, vp, dp, dp, dp, vp, sz, vp]
+        L.lb_step.argtypes = [vp, i]
+        L.lb_observables.argtypes = [vp, ctypes.POINTER(LbObs)]
+        L.lb_get_fields.argtypes = [vp, dp, dp, dp, dp, dp]
+        L.lb_get_state.argtypes = [vp, dp, sz]
+        L.lb_set_state.argtypes = [vp, dp, sz]
+        L.lb_sync.argtypes = [vp]
+        L.lb_destroy.argtypes = [vp]
+        L.lb_destroy.restype = None
+        L.lb_last_error.argtypes = [vp]
+        L.lb_last_error.restype = ctypes.c_char_p
+        L.lb_version.argtypes = []
+        L.lb_version.restype = ctypes.c_char_p
+        for f in ("lb_workspace_size", "lb_init", "lb_step", "lb_observables", "lb_get_fields", "lb_get_state",
+                  "lb_set_state", "lb_sync"):
+            getattr(L, f).restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def make_params(p, precision=LB_FP64):
+    """C struct from a parameter dict (keys as in the C struct; shift_* default to NaN = automatic)."""
+    s = LbParams()
+    s.nx, s.ny = int(p["nx"]), int(p["ny"])
+    s.periodic_y = int(p.get("periodic_y", 0))
+    s.precision = int(p.get("precision", precision))
+    for k in ("tau", "tau_g", "rho0", "G12", "T_down", "T_up", "alpha_g", "body_fx"):
+        setattr(s, k, float(p.get(k, 0.0)))
+    for k in ("Ga", "Gr", "rho_wall"):
+        v = p.get(k, (0.0, 0.0))
+        getattr(s, k)[0], getattr(s, k)[1] = float(v[0]), float(v[1])
+    sr = p.get("shift_rho", (math.nan, math.nan))
+    s.shift_rho[0], s.shift_rho[1] = float(sr[0]), float(sr[1])
+    s.shift_T = float(p.get("shift_T", math.nan))
+    return s
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(rc, h=None):
+    if rc != LB_OK:
+        raise LbError(rc, lib().lb_last_error(h).decode())
+    return rc
+
+
+def workspace_size(params, has_mask=False, precision=LB_FP64):
+    n = ctypes.c_size_t()
+    _check(lib().lb_workspace_size(ctypes.byref(make_params(params, precision)), int(bool(has_mask)), ctypes.byref(n)))
+    return n.value
+
+
+class Lattice:
+    """One lattice on the current CUDA device: workspace tensor + library handle."""
+
+    def __init__(self, params, rho1, rho2, T0, mask=None, precision=LB_FP64, device=None, stream=None):
+        import torch
+
+        self.params = dict(params)
+        self.cp = make_params(self.params, precision)
+        self.nx, self.ny = self.cp.nx, self.cp.ny
+        shape = (self.ny, self.nx)
+        self._r1 = np.ascontiguousarray(np.broadcast_to(rho1, shape), dtype=np.float64)
+        self._r2 = np.ascontiguousarray(np.broadcast_to(rho2, shape), dtype=np.float64)
+        self._t0 = np.ascontiguousarray(np.broadcast_to(T0, shape), dtype=np.float64)
+        self._mask = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.device = dev
+        nbytes = workspace_size(self.params, self._mask is not None, self.cp.precision)
+        with torch.cuda.device(dev):
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._h = ctypes.c_void_p()
+        mptr = None if self._mask is None else self._mask.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().lb_init(ctypes.byref(self._h), ctypes.byref(self.cp), mptr, _dp(self._r1), _dp(self._r2),
+                             _dp(self._t0), ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                             ctypes.c_void_p(self.stream.cuda_stream)))
+
+    # -- C-ABI calls
+    def step(self, n=1):
+        _check(lib().lb_step(self._h, int(n)), self._h)
+        return self
+
+    def observables(self, check=True):
+        o = LbObs()
+        rc = lib().lb_observables(self._h, ctypes.byref(o))
+        if rc not in (LB_OK, LB_EUNSTABLE) or (check and rc != LB_OK):
+            _check(rc, self._h)
+        return {"mass": np.array(o.mass[:]), "mom": np.array(o.mom[:]), "Nu": o.Nu, "E": o.E, "step": o.step,
+                "n_fluid": o.n_fluid, "n_bad": o.n_bad, "status": o.status}
+
+    def fields(self):
+        out = {k: np.zeros((self.ny, self.nx)) for k in ("rho1", "rho2", "T", "ux", "uy")}
+        _check(lib().lb_get_fields(self._h, *(_dp(out[k]) for k in ("rho1", "rho2", "T", "ux", "uy"))), self._h)
+        return out
+
+    def get_state(self):
+        st = np.zeros((27, self.ny, self.nx))
+        _check(lib().lb_get_state(self._h, _dp(st), st.nbytes), self._h)
+        return st
+
+    def set_state(self, state):
+        st = np.ascontiguousarray(state, dtype=np.float64)
+        if st.shape != (27, self.ny, self.nx):
+            raise ValueError("state must have shape (27, ny, nx)")
+        _check(lib().lb_set_state(self._h, _dp(st), st.nbytes), self._h)
+
+    def sync(self):
+        _check(lib().lb_sync(self._h), self._h)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().lb_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle, element by element.
+
+Tolerances (stated per result):
+  FP64 GPU vs oracle: max abs <= 1e-11 on every population and field after 1000 steps of the
+  64 x 64 emulsion; the two differ only by rounding order (fused multiply-adds, pair-difference
+  stencils, reciprocal multiplies) and exp ulps.
+  FP32-shifted vs FP64: norm-relative max|d| / max|ref| <= 1e-4 on rho and T after 200 steps,
+  <= 1e-3 on the time-averaged Nusselt number.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2109_12565_gb300 import build as B
+from paper_2109_12565_gb300 import inputs as I
+from paper_2109_12565_gb300 import lb
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    B.build()
+
+
+def _pair(params, r1, r2, T0, mask=None, precision=lb.LB_FP64, omp=False):
+    g = lb.Lattice(params, r1, r2, T0, mask=mask, precision=precision)
+    o = O.Oracle(params, r1, r2, T0, mask=mask, omp=omp)
+    return g, o
+
+
+def _max_field_diff(fg, fo, keys=("rho1", "rho2", "T", "ux", "uy")):
+    return {k: float(np.abs(fg[k] - fo[k]).max()) for k in keys}
+
+
+def test_fp64_emulsion_64x64_1000_steps_matches_oracle():
+    w = I.emulsion_small()
+    g, o = _pair(w.params, w.rho1, w.rho2, w.T0)
+    g.step(1000)
+    o.step(1000)
+    d_state = np.abs(g.get_state() - o.state).max()
+    d = _max_field_diff(g.fields(), o.fields())
+    assert d_state <= 1e-11, d_state
+    assert max(d.values()) <= 1e-11, d
+    og, oo = g.observables(), o.observables()
+    np.testing.assert_allclose(og["mass"], oo["mass"], rtol=1e-13)
+    np.testing.assert_allclose(og["mom"], oo["mom"], rtol=0, atol=1e-11)
+    assert abs(og["Nu"] - oo["Nu"]) <= 1e-10
+    assert abs(og["E"] - oo["E"]) <= 1e-14
+    assert og["n_fluid"] == oo["n_fluid"] == 64 * 62 and og["n_bad"] == 0
+    # the check is not vacuous: the emulsion moves
+    assert oo["E"] > 1e-10 and abs(oo["Nu"] - 1.0) > 1e-4
+
+
+@pytest.mark.parametrize("nx,ny,periodic,posts", [
+    (37, 21, 0, True),    # ragged in x and y against the 32x16 / 64x16 tiles, posts on both walls
+    (70, 35, 1, False),   # periodic, several tiles with ragged tails
+    (16, 8, 1, False),
+    (8, 8, 0, False),
+    (5, 7, 0, False),     # narrower than the 5-wide stencil: x wraps onto itself
+    (129, 40, 0, True),
+])
+def test_fp64_small_and_ragged_lattices(nx, ny, periodic, posts):
+    R = min(nx, ny) / 5.0
+    w = I.emulsion_small(nx=nx, ny=ny, n_drops=1, R=max(R, 1.5)) if not periodic else None
+    if periodic:
+        y, x = np.mgrid[0:ny, 0:nx]
+        r1 = np.where((x - nx / 2) ** 2 + (y - ny / 2) ** 2 < (min(nx, ny) / 4) ** 2, 1.4, 0.1)
+        r1 = r1 + 1e-3 * (I.uniform(5, nx * ny).reshape(ny, nx) - 0.5)
+        params = dict(I.EMULSION_PARAMS, nx=nx, ny=ny, periodic_y=1, T_down=0.0, T_up=0.0, alpha_g=1e-4)
+        T0 = 0.1 * np.sin(2 * np.pi * x / nx)
+        r2 = 1.5 - r1
+        mask = None
+    else:
+        params, r1, r2, T0 = w.params, w.rho1, w.rho2, w.T0
+        params = dict(params, alpha_g=1e-3)
+        mask = I.posts_mask(nx, ny, 2, 3, 7) if posts else None
+    g, o = _pair(params, r1, r2, T0, mask=mask)
+    for n in (1, 16, 183):
+        g.step(n)
+        o.step(n)
+        d_state = np.abs(g.get_state() - o.state).max()
+        assert d_state <= 1e-12, (n, d_state)
+    d = _max_field_diff(g.fields(), o.fields())
+    assert max(d.values()) <= 1e-12, d
+    og, oo = g.observables(), o.observables()
+    np.testing.assert_allclose(og["mass"], oo["mass"], rtol=1e-13)
+    assert abs(og["Nu"] - oo["Nu"]) <= 1e-10
+    assert og["n_fluid"] == oo["n_fluid"]
+
+
+def test_graph_replay_equals_single_launches_bitwise():
+    """lb_step(n) replays 16-step CUDA graphs plus single launches; the result is bit-identical
+    whatever the split (the kernel is deterministic)."""
+    w = I.emulsion_small()
+    a = lb.Lattice(w.params, w.rho1, w.rho2, w.T0)
+    b = lb.Lattice(w.params, w.rho1, w.rho2, w.T0)
+    a.step(37)
+    for _ in range(37):
+        b.step(1)
+    np.testing.assert_array_equal(a.get_state(), b.get_state())
+    a.step(0)
+    np.testing.assert_array_equal(a.get_state(), b.get_state())
+    assert a.observables()["step"] == 37
+
+
+def test_state_roundtrip_and_restart():
+    """lb_set_state / lb_get_state move the exact FP64 populations; a restart from the oracle's state
+    continues in step with the oracle."""
+    w = I.emulsion_small()
+    o = O.Oracle(w.params, w.rho1, w.rho2, w.T0)
+    o.step(50)
+    g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0)
+    g.set_state(o.state)
+    np.testing.assert_array_equal(g.get_state(), o.state)
+    g.step(50)
+    o.step(50)
+    assert np.abs(g.get_state() - o.state).max() <= 1e-12
+
+
+def test_observables_over_time_match_oracle():
+    w = I.emulsion_small()
+    g, o = _pair(w.params, w.rho1, w.rho2, w.T0)
+    for _ in range(4):
+        og, oo = g.observables(), o.observables()
+        for k in ("Nu", "E"):
+            assert abs(og[k] - oo[k]) <= 1e-10 * max(1.0, abs(oo[k])), (k, og[k], oo[k])
+        np.testing.assert_allclose(og["mass"], oo["mass"], rtol=1e-13)
+        g.step(100)
+        o.step(100)
+
+
+def _norm_rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def test_fp32_shifted_against_fp64_oracle_200_steps():
+    """Precision form: rho and T within 1e-4 (norm-relative) of the FP64 oracle after 200 steps, and
+    the Nusselt number averaged over the 200 post-step states within 1e-3."""
+    w = I.emulsion_small()
+    g, o = _pair(w.params, w.rho1, w.rho2, w.T0, precision=lb.LB_FP32_SHIFTED)
+    nu_g, nu_o = [], []
+    for _ in range(200):
+        g.step(1)
+        o.step(1)
+        nu_g.append(g.observables()["Nu"])
+        nu_o.append(o.observables()["Nu"])
+    fg, fo = g.fields(), o.fields()
+    for k in ("rho1", "rho2", "T"):
+        assert _norm_rel(fg[k], fo[k]) <= 1e-4, (k, _norm_rel(fg[k], fo[k]))
+    assert abs(np.mean(nu_g) - np.mean(nu_o)) <= 1e-3 * abs(np.mean(nu_o))
+    np.testing.assert_allclose(g.observables()["mass"], o.observables()["mass"], rtol=1e-6)
+
+
+def test_fp32_shifted_state_roundtrip():
+    w = I.emulsion_small()
+    g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, precision=lb.LB_FP32_SHIFTED)
+    o = O.Oracle(w.params, w.rho1, w.rho2, w.T0)
+    st = g.get_state()
+    assert np.abs(st - o.state).max() <= 1e-7
+    g.set_state(o.state)
+    assert np.abs(g.get_state() - o.state).max() <= 1e-7
+
+
+@pytest.mark.parametrize("precision,steps,tol", [(lb.LB_FP64, 12, 1e-12), (lb.LB_FP32_SHIFTED, 12, 1e-4)])
+def test_full_size_1024x512_against_oracle(precision, steps, tol):
+    """The 1024 x 512 concentrated emulsion in the launch configuration the benchmark times, checked
+    against the oracle on every node (the OpenMP oracle finishes this in seconds)."""
+    w = I.emulsion_1024x512()
+    g, o = _pair(w.params, w.rho1, w.rho2, w.T0, precision=precision, omp=True)
+    g.step(steps)
+    o.step(steps)
+    fg, fo = g.fields(), o.fields()
+    if precision == lb.LB_FP64:
+        d = _max_field_diff(fg, fo)
+        assert max(d.values()) <= tol, d
+        assert np.abs(g.get_state() - o.state).max() <= tol
+    else:
+        for k in ("rho1", "rho2", "T"):
+            assert _norm_rel(fg[k], fo[k]) <= tol, k
+
+
+def test_unstable_state_is_reported():
+    w = I.emulsion_small(nx=16, ny=16, n_drops=1, R=3.0)
+    g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0)
+    st = g.get_state()
+    st[0, 5, 5] = -10.0  # f_{1,0} at a fluid node: rho_1 < 0
+    g.set_state(st)
+    obs = g.observables(check=False)
+    assert obs["status"] == lb.LB_EUNSTABLE and obs["n_bad"] == 1
+    with pytest.raises(lb.LbError) as e:
+        g.observables()
+    assert e.value.code == lb.LB_EUNSTABLE
+
+
+def test_init_errors():
+    import ctypes
+
+    import torch
+
+    w = I.emulsion_small(nx=16, ny=16, n_drops=1, R=3.0)
+    cp = lb.make_params(w.params)
+    need = lb.workspace_size(w.params)
+    small = torch.empty(need // 2, dtype=torch.uint8, device="cuda")
+    h = ctypes.c_void_p()
+    r = [np.ascontiguousarray(a, dtype=np.float64) for a in (w.rho1, w.rho2, w.T0)]
+    dp = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in r]
+    rc = lb.lib().lb_init(ctypes.byref(h), ctypes.byref(cp), None, *dp, ctypes.c_void_p(small.data_ptr()),
+                          small.numel(), None)
+    assert rc == lb.LB_ENOSPACE
+    assert b"workspace" in lb.lib().lb_last_error(None)
+    with pytest.raises(lb.LbError) as e:
+        lb.Lattice(dict(w.params, periodic_y=1), w.rho1, w.rho2, w.T0, mask=np.ones((16, 16), np.uint8))
+    assert e.value.code == lb.LB_EINVAL
+    bad = w.rho1.copy()
+    bad[4, 4] = 0.0
+    with pytest.raises(lb.LbError) as e:
+        lb.Lattice(w.params, bad, w.rho2, w.T0)
+    assert e.value.code == lb.LB_EINVAL
