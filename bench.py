@@ -81,14 +81,17 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap,utilization.gpu")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
-            time.sleep(0.3)
+            time.sleep(0.5)  # nvidia-smi start-up
+            self.n_before = len(self.samples)
         except Exception:
             self.proc = None
         return self
+
+    n_before = 0
 
     def _read(self):
         for line in self.proc.stdout:
@@ -98,7 +101,7 @@ class ClockSampler:
 
     def __exit__(self, *a):
         if self.proc is not None:
-            time.sleep(0.2)
+            self.n_after = len(self.samples)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -106,6 +109,8 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        # keep the samples taken while the timed loops ran
+        self.samples = self.samples[self.n_before:getattr(self, "n_after", len(self.samples))]
         if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
 
@@ -117,16 +122,15 @@ class ClockSampler:
 
         sm = [num(s[0]) for s in self.samples if num(s[0]) is not None]
         util = [num(s[7]) or 0.0 for s in self.samples]
-        loaded = [num(s[0]) for s in self.samples if (num(s[7]) or 0.0) > 50 and num(s[0]) is not None]
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for s in self.samples:
             for k, n in enumerate(names):
                 if s[3 + k].lower().startswith("active"):
                     reasons.add(n)
-        return {"sm_mhz": statistics.median(loaded or sm), "sm_max_mhz": num(self.samples[0][1]),
-                "reasons": sorted(reasons), "samples": len(self.samples),
-                "samples_under_load": len(loaded), "max_util": max(util) if util else None}
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(self.samples[0][1]),
+                "reasons": sorted(reasons), "samples_in_timed_region": len(self.samples),
+                "max_util": max(util) if util else None}
 
 
 def time_form(w, precision, steps, warmup, flush):
@@ -246,12 +250,14 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forms", default="fp32,fp64", help="comma list of fp32, fp64 (profiling runs)")
+    ap.add_argument("--fp64-steps", type=int, default=0, help="timed FP64 steps (default steps // 4)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -280,57 +286,70 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    forms_req = set(args.forms.split(","))
+    steps64 = args.fp64_steps or max(3, args.steps // 4)
+    r32 = r64 = None
     with ClockSampler(local) as clk:
-        r32 = time_form(w, lb.LB_FP32_SHIFTED, args.steps, args.warmup, flush)
-        r64 = time_form(w, lb.LB_FP64, max(3, args.steps // 4), args.warmup, flush)
+        if "fp32" in forms_req:
+            r32 = time_form(w, lb.LB_FP32_SHIFTED, args.steps, args.warmup, flush)
+        if "fp64" in forms_req:
+            r64 = time_form(w, lb.LB_FP64, steps64, args.warmup, flush)
     torch.cuda.synchronize()
-    t32, t64 = r32["ms_total"], r64["ms_total"]
+    t32 = r32["ms_total"] if r32 else 0.0
+    t64 = r64["ms_total"] if r64 else 0.0
     if dist:
         t = torch.tensor([t32, t64], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t32, t64 = float(t[0]), float(t[1])
-    steps64 = max(3, args.steps // 4)
-    mlups32 = world * N * args.steps / (t32 * 1e3)
-    mlups64 = world * N * steps64 / (t64 * 1e3)
-    e2e = time_e2e(w, lb.LB_FP32_SHIFTED, args.e2e_steps)
-    if dist:
-        t = torch.tensor([e2e["seconds"]], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e["value"] = world * N * args.e2e_steps / float(t[0]) / 1e6
+    mlups32 = world * N * args.steps / (t32 * 1e3) if r32 else None
+    mlups64 = world * N * steps64 / (t64 * 1e3) if r64 else None
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = time_e2e(w, lb.LB_FP32_SHIFTED, args.e2e_steps)
+        if dist:
+            t = torch.tensor([e2e["seconds"]], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e["value"] = world * N * args.e2e_steps / float(t[0]) / 1e6
     if rank != 0:
         dist.destroy_process_group()
         return 0
     peak, peak_kind = _peaks()
     prof = _profile_counters()
     bytes32, bytes64 = 216.0 * N, 432.0 * N  # 27 populations read + written per node
-    ach32 = bytes32 / (r32["ms_per_step"] * 1e-3) / 1e9
-    ach64 = bytes64 / (r64["ms_per_step"] * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s", "frac": ach32 / peak,
-            "traffic": prof.get("fp32_step_dram_bytes_per_launch"), "peak_source": peak_kind,
-            "kernel": "lb_step_kernel<float, shifted> (fused step)", "algorithmic_bytes_per_launch": bytes32}
-    forms = {
-        "fp32_shifted": {"MLUPS": mlups32, "ms_per_step": r32["ms_per_step"], "hbm_frac": ach32 / peak,
-                         "GBps": ach32, "Nu": r32["obs"]["Nu"]},
-        "fp64": {"MLUPS": mlups64, "ms_per_step": r64["ms_per_step"], "hbm_frac": ach64 / peak, "GBps": ach64,
-                 "bound": "alu (FP64 pipe)", "traffic": prof.get("fp64_step_dram_bytes_per_launch"),
-                 "Nu": r64["obs"]["Nu"]},
-        "fp32_over_fp64": mlups32 / mlups64,
-    }
-    dp = prof.get("fp64_dp_flops_per_node")
-    if dp:
-        forms["fp64"]["dp_tflops"] = dp * N / (r64["ms_per_step"] * 1e-3) / 1e12
-        forms["fp64"]["alu_frac_of_nominal"] = forms["fp64"]["dp_tflops"] / FP64_NOMINAL_TFLOPS
+    forms = {}
+    roof = None
+    if r32:
+        ach32 = bytes32 / (r32["ms_per_step"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s", "frac": ach32 / peak,
+                "traffic": prof.get("fp32_step_dram_bytes_per_launch"), "peak_source": peak_kind,
+                "kernel": "lb_step_kernel<float, shifted> (fused step)", "algorithmic_bytes_per_launch": bytes32}
+        forms["fp32_shifted"] = {"MLUPS": mlups32, "ms_per_step": r32["ms_per_step"], "hbm_frac": ach32 / peak,
+                                 "GBps": ach32, "Nu": r32["obs"]["Nu"]}
+    if r64:
+        ach64 = bytes64 / (r64["ms_per_step"] * 1e-3) / 1e9
+        forms["fp64"] = {"MLUPS": mlups64, "ms_per_step": r64["ms_per_step"], "hbm_frac": ach64 / peak,
+                         "GBps": ach64, "bound": "alu (FP64 pipe)",
+                         "traffic": prof.get("fp64_step_dram_bytes_per_launch"), "Nu": r64["obs"]["Nu"]}
+        dp = prof.get("fp64_dp_flops_per_node")
+        if dp:
+            forms["fp64"]["dp_tflops"] = dp * N / (r64["ms_per_step"] * 1e-3) / 1e12
+            forms["fp64"]["alu_frac_of_nominal"] = forms["fp64"]["dp_tflops"] / FP64_NOMINAL_TFLOPS
+    if r32 and r64:
+        forms["fp32_over_fp64"] = mlups32 / mlups64
+    head = r32 or r64
     line = {
-        "metric": METRIC, "value": mlups32, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": r32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "metric": METRIC, "value": mlups32 if r32 else mlups64, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps if r32 else steps64, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32" if r32 else "f64",
+        "data": "synthetic",
         "config": {"workload": w.name, "nx": 1024, "ny": 512, "n_drops": 350, "phi": 0.8, "Ra": 3.6e4,
-                   "form": "fp32_shifted", "l2": "flushed before every timed step (512 MiB write)",
+                   "form": "fp32_shifted" if r32 else "fp64",
+                   "l2": "flushed before every timed step (512 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
         "forms": forms,
         "e2e": e2e,
-        "gpu_launches": args.steps + steps64,
+        "gpu_launches": (args.steps if r32 else 0) + (steps64 if r64 else 0),
         "clocks": clk.summary(),
     }
     if not args.no_cpu_baseline:
