@@ -128,6 +128,25 @@ int lb_get_fields(lb_handle* h, double* rho1, double* rho2, double* T, double* u
 int lb_get_state(lb_handle* h, double* host, size_t bytes);
 int lb_set_state(lb_handle* h, const double* host, size_t bytes);
 
+/* Observables of a state held in the caller's own device memory, for callers that cannot
+ * allocate device memory (no cudaMalloc, no workspace): e.g. a plug-in whose host application owns
+ * every device allocation, or a real-time loop that must not take the device-wide synchronisation
+ * of cudaMalloc / cudaFree.  The paper has no counterpart; it is the lb_observables reduction with
+ * its scratch moved into a fixed device array inside the library.
+ * p: parameters (precision is ignored: the state is FP64).  d_state: device array of 27*nx*ny
+ * doubles in the layout of lb_get_state (27 unpadded planes, x fastest).  d_mask: device nx*ny
+ * bytes or NULL, as the mask given to lb_init.  out: host struct, filled before return (step = 0).
+ * stream: cudaStream_t or NULL; the call synchronises it.
+ * Scratch: a 2 MiB file-scope device array that every GPU loading the library holds until exit;
+ * lattices needing more than 26,212 tiles of 32 x 16 nodes are rejected with LB_EINVAL before any
+ * launch (4096 x 3264 fits, 4096 x 3280 does not).  The first call on a device looks the array up
+ * (cudaGetSymbolAddress) and must come before any stream capture.  All calls on a device share the
+ * array: calls that overlap on the GPU race and must be serialised by the caller.  Allocates
+ * nothing.  Returns LB_OK, LB_EUNSTABLE (out filled), LB_EINVAL or LB_ECUDA; lb_last_error is not
+ * updated. */
+int lb_observables_static(const lb_params* p, const double* d_state, const uint8_t* d_mask, lb_obs* out,
+                          void* stream);
+
 /* Wait for all work of the handle and report any asynchronous CUDA error. */
 int lb_sync(lb_handle* h);
 
