@@ -133,13 +133,19 @@ class ClockSampler:
                 "max_util": max(util) if util else None}
 
 
-def time_form(w, precision, steps, warmup, flush):
+def time_form(w, precision, steps, warmup, flush, tile=-1):
     """Per-step CUDA-event timing of the fused step on the Lattice's stream, L2 flushed before each step."""
     import torch
 
     from paper_2109_12565_gb300 import lb
 
     g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, mask=w.mask, precision=precision)
+    if tile < 0:
+        tile, cand_ms = g.autotune(launches=10)
+    else:
+        g.set_tile(tile)
+        cand_ms = []
+    shape = g.tile_info(tile)
     s = g.stream
     with torch.cuda.stream(s):
         for _ in range(warmup):
@@ -157,7 +163,9 @@ def time_form(w, precision, steps, warmup, flush):
     obs = g.observables()
     g.close()
     return {"ms_total": sum(times), "ms_per_step": sum(times) / steps, "ms_min": min(times),
-            "ms_median": statistics.median(times), "obs": obs}
+            "ms_median": statistics.median(times), "obs": obs,
+            "tile": {"candidate": tile, "tx": shape["tx"], "ty": shape["ty"], "threads": shape["threads"],
+                     "autotune_ms_per_candidate": [round(m, 5) for m in cand_ms]}}
 
 
 def time_e2e(w, precision, steps, obs_every=500):
@@ -258,6 +266,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--forms", default="fp32,fp64", help="comma list of fp32, fp64 (profiling runs)")
     ap.add_argument("--fp64-steps", type=int, default=0, help="timed FP64 steps (default steps // 4)")
+    ap.add_argument("--tile", type=int, default=-1, help="fixed tile candidate instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -291,9 +300,9 @@ def main():
     r32 = r64 = None
     with ClockSampler(local) as clk:
         if "fp32" in forms_req:
-            r32 = time_form(w, lb.LB_FP32_SHIFTED, args.steps, args.warmup, flush)
+            r32 = time_form(w, lb.LB_FP32_SHIFTED, args.steps, args.warmup, flush, args.tile)
         if "fp64" in forms_req:
-            r64 = time_form(w, lb.LB_FP64, steps64, args.warmup, flush)
+            r64 = time_form(w, lb.LB_FP64, steps64, args.warmup, flush, args.tile)
     torch.cuda.synchronize()
     t32 = r32["ms_total"] if r32 else 0.0
     t64 = r64["ms_total"] if r64 else 0.0
@@ -324,12 +333,13 @@ def main():
                 "traffic": prof.get("fp32_step_dram_bytes_per_launch"), "peak_source": peak_kind,
                 "kernel": "lb_step_kernel<float, shifted> (fused step)", "algorithmic_bytes_per_launch": bytes32}
         forms["fp32_shifted"] = {"MLUPS": mlups32, "ms_per_step": r32["ms_per_step"], "hbm_frac": ach32 / peak,
-                                 "GBps": ach32, "Nu": r32["obs"]["Nu"]}
+                                 "GBps": ach32, "Nu": r32["obs"]["Nu"], "tile": r32["tile"]}
     if r64:
         ach64 = bytes64 / (r64["ms_per_step"] * 1e-3) / 1e9
         forms["fp64"] = {"MLUPS": mlups64, "ms_per_step": r64["ms_per_step"], "hbm_frac": ach64 / peak,
                          "GBps": ach64, "bound": "alu (FP64 pipe)",
-                         "traffic": prof.get("fp64_step_dram_bytes_per_launch"), "Nu": r64["obs"]["Nu"]}
+                         "traffic": prof.get("fp64_step_dram_bytes_per_launch"), "Nu": r64["obs"]["Nu"],
+                         "tile": r64["tile"]}
         dp = prof.get("fp64_dp_flops_per_node")
         if dp:
             forms["fp64"]["dp_tflops"] = dp * N / (r64["ms_per_step"] * 1e-3) / 1e12

@@ -128,6 +128,21 @@ int lb_get_fields(lb_handle* h, double* rho1, double* rho2, double* T, double* u
 int lb_get_state(lb_handle* h, double* host, size_t bytes);
 int lb_set_state(lb_handle* h, const double* host, size_t bytes);
 
+/* Tile-shape autotuner of the fused step (not in the paper).  Times every step-kernel tile
+ * candidate of the handle's precision over `launches` launches on the handle's stream and keeps the
+ * fastest for later lb_step calls.  Each trial reads the current state and writes the inactive
+ * buffer, so the state and the step counter do not change.  chosen (may be NULL) receives the
+ * winning candidate; ms_per_candidate (may be NULL, n_slots entries) the mean milliseconds per
+ * launch of each candidate.  Synchronous. */
+int lb_autotune(lb_handle* h, int launches, int* chosen, double* ms_per_candidate, int n_slots);
+
+/* Use tile candidate `candidate` for later lb_step calls (LB_EINVAL if out of range). */
+int lb_set_tile(lb_handle* h, int candidate);
+
+/* Shape of tile candidate `candidate` (-1: the current one): tile width tx, height ty and threads
+ * per CTA.  Returns the number of candidates (>= 1) or LB_EINVAL. */
+int lb_tile_info(const lb_handle* h, int candidate, int* tx, int* ty, int* threads);
+
 /* Observables of a state held in the caller's own device memory, for callers that cannot
  * allocate device memory (no cudaMalloc, no workspace): e.g. a plug-in whose host application owns
  * every device allocation, or a real-time loop that must not take the device-wide synchronisation

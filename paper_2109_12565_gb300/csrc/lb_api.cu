@@ -13,70 +13,16 @@
 #include <vector>
 
 #include "lb_cfg.h"
+#include "lb_host.h"
 #include "tlb.h"
 
 using namespace tlb;
 
 namespace {
 
-constexpr size_t kAlign = 256;
 constexpr int kGraphLen = 16;  // steps per captured graph (even: replay keeps the buffer parity)
 
 thread_local char g_err[512] = "no error";
-
-size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-struct Layout {
-  int pitch = 0;
-  size_t elem = 0, buf_bytes = 0, mask_off = 0, part_off = 0, obs_off = 0, total = 0;
-  int n_blocks = 0;
-};
-
-int tile_x(int precision) { return precision == LB_FP64 ? Tile<double>::TX : Tile<float>::TX; }
-int tile_y(int precision) { return precision == LB_FP64 ? Tile<double>::TY : Tile<float>::TY; }
-
-const char* check_params(const lb_params* p) {
-  if (!p) return "params is NULL";
-  if (p->nx < 1 || p->ny < 1) return "nx and ny must be >= 1";
-  if ((long long)p->nx * p->ny > (1LL << 31) - 1) return "nx * ny must fit in 31 bits";
-  if (!p->periodic_y && p->ny < 3) return "walls (periodic_y = 0) need ny >= 3";
-  if (p->precision != LB_FP64 && p->precision != LB_FP32_SHIFTED) return "precision must be LB_FP64 or LB_FP32_SHIFTED";
-  if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return "tau must be finite and > 1/2";
-  if (!(p->tau_g > 0.5) || !std::isfinite(p->tau_g)) return "tau_g must be finite and > 1/2";
-  if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0)) return "rho0 must be finite and > 0";
-  const double vals[] = {p->G12, p->Ga[0], p->Ga[1], p->Gr[0], p->Gr[1], p->T_down, p->T_up, p->alpha_g, p->body_fx};
-  for (double v : vals)
-    if (!std::isfinite(v)) return "coupling, temperature and force parameters must be finite";
-  if (!(p->rho_wall[0] > 0.0) || !(p->rho_wall[1] > 0.0) || !std::isfinite(p->rho_wall[0]) ||
-      !std::isfinite(p->rho_wall[1]))
-    return "rho_wall must be finite and > 0";
-  return nullptr;
-}
-
-Layout layout_for(const lb_params* p, int has_mask) {
-  Layout L;
-  L.elem = p->precision == LB_FP64 ? 8 : 4;
-  const int per_row = (int)(128 / L.elem);
-  L.pitch = (p->nx + per_row - 1) / per_row * per_row;
-  const size_t plane = (size_t)L.pitch * p->ny;
-  L.buf_bytes = round_up(27 * plane * L.elem, kAlign);
-  // the inactive buffer doubles as staging for init (3 planes) and fields (5 planes) of doubles
-  const size_t staging = (size_t)p->nx * p->ny * 5 * sizeof(double);
-  if (staging > L.buf_bytes) L.buf_bytes = round_up(staging, kAlign);
-  size_t off = 2 * L.buf_bytes;
-  L.mask_off = off;
-  if (has_mask) off += round_up((size_t)p->nx * p->ny, kAlign);
-  const int tx = tile_x(p->precision), ty = tile_y(p->precision);
-  L.n_blocks = ((p->nx + tx - 1) / tx) * ((p->ny + ty - 1) / ty);
-  L.part_off = off;
-  off += round_up((size_t)L.n_blocks * kObsSlots * sizeof(double), kAlign);
-  L.obs_off = off;
-  off += round_up(kObsOut * sizeof(double), kAlign);
-  L.total = off;
-  return L;
-}
-
-double psi_exp_host(double rho, double rho0) { return rho0 * (1.0 - std::exp(-rho / rho0)); }
 
 }  // namespace
 
@@ -91,6 +37,7 @@ struct lb_handle {
   int cur = 0;
   long long step = 0;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int tile = 0;  // step-kernel tile candidate (see lb_autotune)
   char err[512] = "no error";
 };
 
@@ -112,53 +59,25 @@ int fail(lb_handle* h, int code, const char* fmt, ...) {
   } while (0)
 
 cudaError_t launch(const lb_handle* h, int mode, const void* fin, void* fout, double* aux, cudaStream_t s) {
+  if (mode == MODE_STEP)
+    return h->p.precision == LB_FP64 ? launch_step_tile_f64(h->tile, h->cfg, fin, fout, s)
+                                     : launch_step_tile_f32(h->tile, h->cfg, fin, fout, s);
   return h->p.precision == LB_FP64 ? launch_f64(mode, h->cfg, fin, fout, aux, s)
                                    : launch_f32(mode, h->cfg, fin, fout, aux, s);
 }
 
-void fill_cfg(lb_handle* h, const uint8_t* d_mask) {
-  const lb_params& p = h->p;
-  StepCfg& c = h->cfg;
-  c.nx = p.nx;
-  c.ny = p.ny;
-  c.pitch = h->L.pitch;
-  c.periodic_y = p.periodic_y ? 1 : 0;
-  c.plane = (long long)h->L.pitch * p.ny;
-  c.mask = d_mask;
-  c.tau = p.tau;
-  c.inv_tau = 1.0 / p.tau;
-  c.inv_tau_g = 1.0 / p.tau_g;
-  c.rho0 = p.rho0;
-  c.inv_rho0 = 1.0 / p.rho0;
-  c.gx = p.G12 / (p.rho0 * p.rho0);
-  for (int l = 0; l < 2; ++l) {
-    // Fig. 1b weights per shell |c|^2 = 1, 2, 4, 5, 8: w = 1/9, 1/36, 0, 0, 0; p = 4/63, 4/135, 1/180, 2/945, 1/15120
-    c.a1[l] = p.Ga[l] / 9.0 + p.Gr[l] * 4.0 / 63.0;
-    c.a2[l] = p.Ga[l] / 36.0 + p.Gr[l] * 4.0 / 135.0;
-    c.a4x2[l] = 2.0 * p.Gr[l] / 180.0;
-    c.a5[l] = p.Gr[l] * 2.0 / 945.0;
-    c.a8x2[l] = 2.0 * p.Gr[l] / 15120.0;
-    c.rho_w[l] = p.rho_wall[l];
-    c.psi_w[l] = psi_exp_host(p.rho_wall[l], p.rho0);
-  }
-  c.T_down = p.T_down;
-  c.T_up = p.T_up;
-  c.alpha_g = p.alpha_g;
-  c.body_fx = p.body_fx;
-  c.rho_bar[0] = c.rho_bar[1] = c.T_bar = 0.0;
-  if (p.precision == LB_FP32_SHIFTED) {
-    c.rho_bar[0] = p.shift_rho[0];
-    c.rho_bar[1] = p.shift_rho[1];
-    c.T_bar = p.shift_T;
-  }
-  c.kappa = (p.tau_g - 0.5) / 3.0;
-  c.H = (double)(p.ny - 2);
+int tile_count(const lb_handle* h) { return h->p.precision == LB_FP64 ? tile_count_f64() : tile_count_f32(); }
+
+void drop_graphs(lb_handle* h) {
+  for (auto& g : h->gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
 }
 
-bool is_solid_host(const lb_params& p, const uint8_t* mask, int x, int y) {
-  if (!p.periodic_y && (y == 0 || y == p.ny - 1)) return true;
-  return mask && mask[(size_t)y * p.nx + x];
-}
+void fill_cfg(lb_handle* h, const uint8_t* d_mask) { h->cfg = make_stepcfg(h->p, h->L.pitch, d_mask); }
+
 
 int build_graph(lb_handle* h, int parity) {
   cudaGraph_t g = nullptr;
@@ -216,26 +135,10 @@ int lb_init(lb_handle** out, const lb_params* pin, const uint8_t* mask, const do
   }
   // initial fields: finite, positive densities at fluid nodes; shifts default to the fluid means
   const size_t N = (size_t)p.nx * p.ny;
-  double sum1 = 0.0, sum2 = 0.0;
-  size_t nf = 0;
-  for (int y = 0; y < p.ny; ++y)
-    for (int x = 0; x < p.nx; ++x) {
-      if (is_solid_host(p, mask, x, y)) continue;
-      const size_t n = (size_t)y * p.nx + x;
-      if (!(rho1[n] > 0.0) || !(rho2[n] > 0.0) || !std::isfinite(rho1[n]) || !std::isfinite(rho2[n]) ||
-          !std::isfinite(T0[n]))
-        return fail(nullptr, LB_EINVAL, "initial densities must be finite and > 0 and T0 finite (node %d,%d)", x, y);
-      sum1 += rho1[n];
-      sum2 += rho2[n];
-      ++nf;
-    }
-  if (nf == 0) return fail(nullptr, LB_EINVAL, "the lattice has no fluid node");
-  if (p.precision == LB_FP32_SHIFTED) {
-    if (std::isnan(p.shift_rho[0])) p.shift_rho[0] = sum1 / (double)nf;
-    if (std::isnan(p.shift_rho[1])) p.shift_rho[1] = sum2 / (double)nf;
-    if (std::isnan(p.shift_T)) p.shift_T = 0.5 * (p.T_down + p.T_up);
-    if (!std::isfinite(p.shift_rho[0]) || !std::isfinite(p.shift_rho[1]) || !std::isfinite(p.shift_T))
-      return fail(nullptr, LB_EINVAL, "shift constants must be finite (or NaN for the defaults)");
+  {
+    char why[256];
+    if (const char* bad = prepare_fields(p, mask, rho1, rho2, T0, why, sizeof why))
+      return fail(nullptr, LB_EINVAL, "%s", bad);
   }
 
   lb_handle* h = new (std::nothrow) lb_handle();
@@ -359,6 +262,71 @@ int lb_set_state(lb_handle* h, const double* host, size_t bytes) {
   return LB_OK;
 }
 
+int lb_autotune(lb_handle* h, int launches, int* chosen, double* ms_per_candidate, int n_slots) {
+  if (!h) return fail(nullptr, LB_EINVAL, "handle is NULL");
+  if (launches < 1) return fail(h, LB_EINVAL, "launches must be >= 1");
+  const int n = tile_count(h);
+  if (ms_per_candidate && n_slots < n) return fail(h, LB_EINVAL, "ms_per_candidate needs %d slots", n);
+  cudaEvent_t e0, e1;
+  CUDA_TRY(h, cudaEventCreate(&e0));
+  CUDA_TRY(h, cudaEventCreate(&e1));
+  const int saved = h->tile;
+  int best = saved;
+  float best_ms = 0.0f;
+  int rc = LB_OK;
+  for (int k = 0; k < n && rc == LB_OK; ++k) {
+    h->tile = k;
+    // every trial reads the current state and writes the inactive buffer: the state does not advance
+    cudaError_t e = launch(h, MODE_STEP, h->buf[h->cur], h->buf[h->cur ^ 1], nullptr, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int r = 0; r < launches && e == cudaSuccess; ++r)
+      e = launch(h, MODE_STEP, h->buf[h->cur], h->buf[h->cur ^ 1], nullptr, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      rc = fail(h, LB_ECUDA, "autotune candidate %d: %s", k, cudaGetErrorString(e));
+      break;
+    }
+    ms /= (float)launches;
+    if (ms_per_candidate) ms_per_candidate[k] = ms;
+    if (k == 0 || ms < best_ms) {
+      best_ms = ms;
+      best = k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != LB_OK) {
+    h->tile = saved;
+    return rc;
+  }
+  if (best != saved) drop_graphs(h);
+  h->tile = best;
+  if (chosen) *chosen = best;
+  return LB_OK;
+}
+
+int lb_set_tile(lb_handle* h, int candidate) {
+  if (!h) return fail(nullptr, LB_EINVAL, "handle is NULL");
+  if (candidate < 0 || candidate >= tile_count(h)) return fail(h, LB_EINVAL, "tile candidate out of range");
+  if (candidate != h->tile) drop_graphs(h);
+  h->tile = candidate;
+  return LB_OK;
+}
+
+int lb_tile_info(const lb_handle* h, int candidate, int* tx, int* ty, int* threads) {
+  if (!h) return fail(nullptr, LB_EINVAL, "handle is NULL");
+  if (candidate < 0) candidate = h->tile;
+  if (candidate >= tile_count(h)) return LB_EINVAL;
+  const TileChoice t = h->p.precision == LB_FP64 ? tile_info_f64(candidate) : tile_info_f32(candidate);
+  if (tx) *tx = t.tx;
+  if (ty) *ty = t.ty;
+  if (threads) *threads = t.tx * t.by;
+  return tile_count(h);
+}
+
 int lb_sync(lb_handle* h) {
   if (!h) return fail(nullptr, LB_EINVAL, "handle is NULL");
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -371,8 +339,7 @@ void lb_destroy(lb_handle* h) {
   if (h->stream || h->cap) {
     if (h->stream) cudaStreamSynchronize(h->stream);
   }
-  for (auto& g : h->gexec)
-    if (g) cudaGraphExecDestroy(g);
+  drop_graphs(h);
   if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
 }

@@ -57,6 +57,17 @@ cudaError_t plane_get_f64(const StepCfg& c, int k, const void* buf, double* out,
 cudaError_t plane_get_f32(const StepCfg& c, int k, const void* buf, double* out, cudaStream_t s);
 cudaError_t plane_put_f64(const StepCfg& c, int k, const double* in, void* buf, cudaStream_t s);
 cudaError_t plane_put_f32(const StepCfg& c, int k, const double* in, void* buf, cudaStream_t s);
+// Step-kernel tile candidates for the autotuner: tile TX x TY nodes, TX * BY threads, at least MINB
+// resident CTAs per SM requested from the compiler.  Candidate 0 is the default.
+struct TileChoice {
+  int tx, ty, by, minb;
+};
+int tile_count_f64();
+int tile_count_f32();
+TileChoice tile_info_f64(int k);
+TileChoice tile_info_f32(int k);
+cudaError_t launch_step_tile_f64(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
+cudaError_t launch_step_tile_f32(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
 // Deterministic final reduction of n_blocks partials into kObsOut doubles.
 cudaError_t obs_finalize(const StepCfg& c, const double* partials, int n_blocks, double* out, cudaStream_t s);
 

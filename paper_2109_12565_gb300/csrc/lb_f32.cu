@@ -10,6 +10,28 @@ cudaError_t launch_f32(int mode, const StepCfg& c, const void* fin, void* fout, 
   return launch_impl<float, true>(mode, c, fin, fout, aux, s);
 }
 
+namespace {
+using StepFn = cudaError_t (*)(const StepCfg&, const void*, void*, cudaStream_t);
+struct Cand {
+  TileChoice t;
+  StepFn fn;
+};
+const Cand kCands[] = {
+    {{64, 16, 4, 3}, launch_step_shape<float, true, 64, 16, 4, 3>},
+    {{32, 16, 8, 3}, launch_step_shape<float, true, 32, 16, 8, 3>},
+    {{64, 32, 8, 2}, launch_step_shape<float, true, 64, 32, 8, 2>},
+    {{128, 16, 2, 3}, launch_step_shape<float, true, 128, 16, 2, 3>},
+    {{64, 8, 4, 4}, launch_step_shape<float, true, 64, 8, 4, 4>},
+    {{32, 32, 8, 3}, launch_step_shape<float, true, 32, 32, 8, 3>},
+};
+}  // namespace
+
+int tile_count_f32() { return (int)(sizeof kCands / sizeof kCands[0]); }
+TileChoice tile_info_f32(int k) { return kCands[k].t; }
+cudaError_t launch_step_tile_f32(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s) {
+  return kCands[k].fn(c, fin, fout, s);
+}
+
 cudaError_t init_f32(const StepCfg& c, const double* fields, void* buf, cudaStream_t s) {
   lb_init_kernel<float, true><<<rows_grid(c), 128, 0, s>>>(fields, static_cast<float*>(buf), c);
   return cudaGetLastError();

@@ -8,6 +8,25 @@ cudaError_t launch_f64(int mode, const StepCfg& c, const void* fin, void* fout, 
   return launch_impl<double, false>(mode, c, fin, fout, aux, s);
 }
 
+namespace {
+using StepFn = cudaError_t (*)(const StepCfg&, const void*, void*, cudaStream_t);
+struct Cand {
+  TileChoice t;
+  StepFn fn;
+};
+const Cand kCands[] = {
+    {{32, 16, 8, 2}, launch_step_shape<double, false, 32, 16, 8, 2>},
+    {{64, 16, 4, 2}, launch_step_shape<double, false, 64, 16, 4, 2>},
+    {{32, 32, 8, 2}, launch_step_shape<double, false, 32, 32, 8, 2>},
+};
+}  // namespace
+
+int tile_count_f64() { return (int)(sizeof kCands / sizeof kCands[0]); }
+TileChoice tile_info_f64(int k) { return kCands[k].t; }
+cudaError_t launch_step_tile_f64(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s) {
+  return kCands[k].fn(c, fin, fout, s);
+}
+
 cudaError_t init_f64(const StepCfg& c, const double* fields, void* buf, cudaStream_t s) {
   lb_init_kernel<double, false><<<rows_grid(c), 128, 0, s>>>(fields, static_cast<double*>(buf), c);
   return cudaGetLastError();

@@ -18,11 +18,15 @@
 //            (Eq. shift, u^(H)), BGK relaxation (Eqs. BGK, LBMg) and the
 //            push-store of f*(x) to x + c_i of the other buffer, bouncing back
 //            (Sec. 2.2) or anti-bouncing (thermal walls) when x + c_i is solid.
+// A CTA whose tile and 1-node ring hold no solid node and need no periodic
+// wrap takes a fast path: every store is an unconditional constant offset.
 // Writes of direction i from a warp land on one contiguous row shifted by
 // c_i; each destination slot has exactly one writer per step.
 #pragma once
 #include <math.h>
 #include <stdint.h>
+
+#include <atomic>
 
 #include "lb_cfg.h"
 
@@ -35,6 +39,70 @@ __host__ __device__ constexpr int oppq(int i) { return i == 0 ? 0 : (i <= 4 ? ((
 // D2Q9 weights w_i (Fig. 1b).
 template <class C> __host__ __device__ constexpr C wq(int i) { return i == 0 ? C(4) / C(9) : (i <= 4 ? C(1) / C(9) : C(1) / C(36)); }
 
+// Kernel constants in the compute precision C (rounded once on the host).
+template <class C> struct KParams {
+  int nx, ny, pitch, periodic_y;
+  int plane;  // elements per population plane (27 * plane < 2^31 is checked on the host)
+  const uint8_t* mask;
+  C tau, inv_tau, inv_tau_g, rho0, inv_rho0, gx;
+  C a1[2], a2[2], a4x2[2], a5[2], a8x2[2];
+  C rho_w[2], psi_w[2];
+  C drho_w[2];  // rho_w - rho_bar (shared memory holds density deviations)
+  C T_down, T_up, alpha_g, body_fx;
+  C rho_bar[2], T_bar;
+  C twoTw_down, twoTw_up;  // 2 (T_w - T_bar) for the anti-bounce-back
+  int tau_is_one;          // tau == 1: f* = f^eq exactly, the relaxation is skipped
+  int tau_g_is_one;        // tau_g == 1: g* = g^eq
+  double rho_w_d[2], T_down_d, T_up_d;  // field output at solid nodes
+};
+
+template <class C> inline KParams<C> make_kparams(const StepCfg& c) {
+  KParams<C> k;
+  k.nx = c.nx;
+  k.ny = c.ny;
+  k.pitch = c.pitch;
+  k.periodic_y = c.periodic_y;
+  k.plane = (int)c.plane;
+  k.mask = c.mask;
+  k.tau = C(c.tau);
+  k.inv_tau = C(c.inv_tau);
+  k.inv_tau_g = C(c.inv_tau_g);
+  k.rho0 = C(c.rho0);
+  k.inv_rho0 = C(c.inv_rho0);
+  k.gx = C(c.gx);
+  for (int l = 0; l < 2; ++l) {
+    k.a1[l] = C(c.a1[l]);
+    k.a2[l] = C(c.a2[l]);
+    k.a4x2[l] = C(c.a4x2[l]);
+    k.a5[l] = C(c.a5[l]);
+    k.a8x2[l] = C(c.a8x2[l]);
+    k.rho_w[l] = C(c.rho_w[l]);
+    k.psi_w[l] = C(c.psi_w[l]);
+    k.drho_w[l] = C(c.rho_w[l] - c.rho_bar[l]);
+    k.rho_bar[l] = C(c.rho_bar[l]);
+    k.rho_w_d[l] = c.rho_w[l];
+  }
+  k.T_down = C(c.T_down);
+  k.T_up = C(c.T_up);
+  k.alpha_g = C(c.alpha_g);
+  k.body_fx = C(c.body_fx);
+  k.T_bar = C(c.T_bar);
+  k.twoTw_down = C(2.0 * (c.T_down - c.T_bar));
+  k.twoTw_up = C(2.0 * (c.T_up - c.T_bar));
+  k.tau_is_one = (c.tau == 1.0) ? 1 : 0;
+  k.tau_g_is_one = (c.inv_tau_g == 1.0) ? 1 : 0;
+  k.T_down_d = c.T_down;
+  k.T_up_d = c.T_up;
+  return k;
+}
+
+// Population load: the read-only path inside one step per launch, L2-coherent loads (ld.global.cg)
+// when the same launch rewrites the buffers (persistent multi-step kernels).
+template <bool CG, class S> __device__ __forceinline__ S ld_pop(const S* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
 __device__ __forceinline__ int wrap_any(int a, int n) {
   int r = a % n;
   return r < 0 ? r + n : r;
@@ -45,8 +113,13 @@ template <> __device__ __forceinline__ double psi_exp<double>(double rho, double
   return rho0 * (1.0 - exp(-rho * inv_rho0));
 }
 template <> __device__ __forceinline__ float psi_exp<float>(float rho, float rho0, float inv_rho0) {
-  return -rho0 * expm1f(-rho * inv_rho0);
+  return rho0 - rho0 * __expf(-rho * inv_rho0);
 }
+
+// 1 / x: IEEE in FP64, the fast approximate division in FP32.
+template <class C> __device__ __forceinline__ C recip(C x);
+template <> __device__ __forceinline__ double recip<double>(double x) { return 1.0 / x; }
+template <> __device__ __forceinline__ float recip<float>(float x) { return __fdividef(1.0f, x); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -54,163 +127,247 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-template <class S, class C, bool SHIFT, int MODE, int TX, int TY, int BY>
-__global__ void __launch_bounds__(TX * BY)
-lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const StepCfg cfg, double* __restrict__ aux) {
-  constexpr int RX = TX + 4, RY = TY + 4, NT = TX * BY;
-  constexpr bool NEED_T = (MODE != MODE_STEP);
-  __shared__ C s_rho[2][RY][RX];
-  __shared__ C s_psi[2][RY][RX];
-  __shared__ C s_T[NEED_T ? RY : 1][NEED_T ? RX : 1];
-  __shared__ unsigned char s_solid[RY][RX];
+template <class C, int TX, int TY, bool NEED_T> struct TileSmem {
+  static constexpr int RX = TX + 4, RY = TY + 4;
+  C rho[2][RY][RX];  // density deviations rho_l - rho_bar_l (rho_bar = 0 in FP64)
+  C psi[2][RY][RX];
+  C jx[TY][TX], jy[TY][TX];  // bare momentum of the tile's own nodes
+  C T[NEED_T ? RY : 1][NEED_T ? RX : 1];
+  unsigned char solid[RY][RX];
+};
 
-  const int nx = cfg.nx, ny = cfg.ny, pitch = cfg.pitch;
-  const long long plane = cfg.plane;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int tid = threadIdx.y * TX + threadIdx.x;
-  const C rho0 = C(cfg.rho0), inv_rho0 = C(cfg.inv_rho0);
-  const C rb0 = SHIFT ? C(cfg.rho_bar[0]) : C(0), rb1 = SHIFT ? C(cfg.rho_bar[1]) : C(0);
-  const C Tb = SHIFT ? C(cfg.T_bar) : C(0);
-
-  // ---------------- phase A: densities and pseudo-potentials on the tile + 2-node ring
+// Phase A on one tile: rho, psi (and T for the observables) on the tile + 2-node ring.
+// Returns (CTA-uniform) whether the fast path applies.
+template <class S, class C, bool SHIFT, bool NEED_T, int TX, int TY, int NT, bool CG>
+__device__ __forceinline__ bool tile_phase_a(const S* __restrict__ fin, const KParams<C>& kp, int x0, int y0,
+                                             TileSmem<C, TX, TY, NEED_T>& sm, int tid) {
+  constexpr int RX = TX + 4, RY = TY + 4;
+  const int nx = kp.nx, ny = kp.ny, pitch = kp.pitch, plane = kp.plane;
+  const bool small_x = nx < TX + 4, small_y = ny < TY + 4;
+  const C rb0 = SHIFT ? kp.rho_bar[0] : C(0), rb1 = SHIFT ? kp.rho_bar[1] : C(0);
+  int ring_solid = 0;
   for (int r = tid; r < RX * RY; r += NT) {
     const int ry = r / RX, rx = r - ry * RX;
-    const int gx = wrap_any(x0 + rx - 2, nx);
+    int gx = x0 + rx - 2;
+    if (small_x) gx = wrap_any(gx, nx);
+    else gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
     int gy = y0 + ry - 2;
     bool solid;
-    if (cfg.periodic_y) {
-      gy = wrap_any(gy, ny);
-      solid = cfg.mask != nullptr && cfg.mask[(long long)gy * nx + gx] != 0;
+    if (kp.periodic_y) {
+      if (small_y) gy = wrap_any(gy, ny);
+      else gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+      solid = kp.mask != nullptr && kp.mask[gy * nx + gx] != 0;
     } else {
-      solid = (gy <= 0 || gy >= ny - 1) || (cfg.mask != nullptr && cfg.mask[(long long)gy * nx + gx] != 0);
+      solid = (gy <= 0 || gy >= ny - 1) || (kp.mask != nullptr && kp.mask[gy * nx + gx] != 0);
     }
+    if (solid && rx >= 1 && rx <= TX + 2 && ry >= 1 && ry <= TY + 2) ring_solid = 1;
     if (solid) {
-      s_rho[0][ry][rx] = C(cfg.rho_w[0]);
-      s_rho[1][ry][rx] = C(cfg.rho_w[1]);
-      s_psi[0][ry][rx] = C(cfg.psi_w[0]);
-      s_psi[1][ry][rx] = C(cfg.psi_w[1]);
-      if (NEED_T) s_T[NEED_T ? ry : 0][NEED_T ? rx : 0] = C(2 * gy < ny ? cfg.T_down : cfg.T_up);
-      s_solid[ry][rx] = 1;
+      sm.rho[0][ry][rx] = kp.drho_w[0];
+      sm.rho[1][ry][rx] = kp.drho_w[1];
+      sm.psi[0][ry][rx] = kp.psi_w[0];
+      sm.psi[1][ry][rx] = kp.psi_w[1];
+      if constexpr (NEED_T) sm.T[ry][rx] = (2 * gy < ny) ? kp.T_down : kp.T_up;
+      sm.solid[ry][rx] = 1;
     } else {
-      const long long idx = (long long)gy * pitch + gx;
-      C r1 = C(0), r2 = C(0);
+      const S* src = fin + (gy * pitch + gx);
+      C f[9], h[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
-        r1 += C(fin[i * plane + idx]);
-        r2 += C(fin[(9 + i) * plane + idx]);
+        f[i] = C(ld_pop<CG>(src + i * plane));
+        h[i] = C(ld_pop<CG>(src + (9 + i) * plane));
       }
-      r1 += rb0;
-      r2 += rb1;
-      s_rho[0][ry][rx] = r1;
-      s_rho[1][ry][rx] = r2;
-      s_psi[0][ry][rx] = psi_exp<C>(r1, rho0, inv_rho0);
-      s_psi[1][ry][rx] = psi_exp<C>(r2, rho0, inv_rho0);
-      if (NEED_T) {
+      C d1 = C(0), d2 = C(0);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        d1 += f[i];
+        d2 += h[i];
+      }
+      sm.rho[0][ry][rx] = d1;
+      sm.rho[1][ry][rx] = d2;
+      sm.psi[0][ry][rx] = psi_exp<C>(d1 + rb0, kp.rho0, kp.inv_rho0);
+      sm.psi[1][ry][rx] = psi_exp<C>(d2 + rb1, kp.rho0, kp.inv_rho0);
+      if (rx >= 2 && rx < TX + 2 && ry >= 2 && ry < TY + 2) {
+        sm.jx[ry - 2][rx - 2] = (f[1] - f[3] + f[5] - f[6] - f[7] + f[8]) + (h[1] - h[3] + h[5] - h[6] - h[7] + h[8]);
+        sm.jy[ry - 2][rx - 2] = (f[2] - f[4] + f[5] + f[6] - f[7] - f[8]) + (h[2] - h[4] + h[5] + h[6] - h[7] - h[8]);
+      }
+      if constexpr (NEED_T) {
         C t = C(0);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) t += C(fin[(18 + i) * plane + idx]);
-        s_T[NEED_T ? ry : 0][NEED_T ? rx : 0] = t + Tb;
+        for (int i = 0; i < 9; ++i) t += C(ld_pop<CG>(src + (18 + i) * plane));
+        sm.T[ry][rx] = t + (SHIFT ? kp.T_bar : C(0));
       }
-      s_solid[ry][rx] = 0;
+      sm.solid[ry][rx] = 0;
     }
   }
-  __syncthreads();
+  const int any = __syncthreads_or(ring_solid);
+  const bool no_wrap_x = x0 >= 1 && x0 + TX + 1 <= nx;
+  const bool no_wrap_y = !kp.periodic_y || (y0 >= 1 && y0 + TY + 1 <= ny);
+  return !any && no_wrap_x && no_wrap_y;
+}
 
-  // ---------------- phase B: one fluid node per (thread, k)
-  const C inv_tau = C(cfg.inv_tau), inv_tau_g = C(cfg.inv_tau_g), tau = C(cfg.tau);
-  const C gxc = C(cfg.gx), ag = C(cfg.alpha_g), bfx = C(cfg.body_fx);
-  double acc[kObsSlots];
-  if (MODE == MODE_OBS) {
+// Interaction + external forces at the node whose shared-memory centre is (cx, cy).
+template <class C, int TX, int TY, bool NEED_T>
+__device__ __forceinline__ void node_forces(const TileSmem<C, TX, TY, NEED_T>& sm, const KParams<C>& kp, int cx, int cy,
+                                            C r1, C r2, C T, C Fx[2], C Fy[2]) {
 #pragma unroll
-    for (int v = 0; v < kObsSlots; ++v) acc[v] = 0.0;
+  for (int l = 0; l < 2; ++l) {
+    const int m = 1 - l;
+    // Eq. FAB on rho: -G12/rho0^2 rho_l(x) sum_{NN} w_i rho_m(x + c_i) c_i, as pair differences
+    const C e10 = sm.rho[m][cy][cx + 1] - sm.rho[m][cy][cx - 1];
+    const C e01 = sm.rho[m][cy + 1][cx] - sm.rho[m][cy - 1][cx];
+    const C e11 = sm.rho[m][cy + 1][cx + 1] - sm.rho[m][cy - 1][cx - 1];
+    const C em1 = sm.rho[m][cy + 1][cx - 1] - sm.rho[m][cy - 1][cx + 1];
+    const C w1 = C(1) / C(9), w2 = C(1) / C(36);
+    const C crx = w1 * e10 + w2 * (e11 - em1);
+    const C cry = w1 * e01 + w2 * (e11 + em1);
+    const C rl = (l == 0) ? r1 : r2;
+    // Eqs. FintAttrattive + FintRepulsive: -psi_l(x) sum_{24 links} (G^a w_i + G^r p_i) psi_l(x + c_i) c_i
+    const C d10 = sm.psi[l][cy][cx + 1] - sm.psi[l][cy][cx - 1];
+    const C d01 = sm.psi[l][cy + 1][cx] - sm.psi[l][cy - 1][cx];
+    const C d11 = sm.psi[l][cy + 1][cx + 1] - sm.psi[l][cy - 1][cx - 1];
+    const C dm1 = sm.psi[l][cy + 1][cx - 1] - sm.psi[l][cy - 1][cx + 1];
+    const C d20 = sm.psi[l][cy][cx + 2] - sm.psi[l][cy][cx - 2];
+    const C d02 = sm.psi[l][cy + 2][cx] - sm.psi[l][cy - 2][cx];
+    const C d12 = sm.psi[l][cy + 2][cx + 1] - sm.psi[l][cy - 2][cx - 1];
+    const C dm12 = sm.psi[l][cy + 2][cx - 1] - sm.psi[l][cy - 2][cx + 1];
+    const C d21 = sm.psi[l][cy + 1][cx + 2] - sm.psi[l][cy - 1][cx - 2];
+    const C dm21 = sm.psi[l][cy + 1][cx - 2] - sm.psi[l][cy - 1][cx + 2];
+    const C d22 = sm.psi[l][cy + 2][cx + 2] - sm.psi[l][cy - 2][cx - 2];
+    const C dm22 = sm.psi[l][cy + 2][cx - 2] - sm.psi[l][cy - 2][cx + 2];
+    const C sx = kp.a1[l] * d10 + kp.a2[l] * (d11 - dm1) + kp.a4x2[l] * d20 +
+                 kp.a5[l] * (d12 - dm12 + C(2) * (d21 - dm21)) + kp.a8x2[l] * (d22 - dm22);
+    const C sy = kp.a1[l] * d01 + kp.a2[l] * (d11 + dm1) + kp.a4x2[l] * d02 +
+                 kp.a5[l] * (C(2) * (d12 + dm12) + d21 + dm21) + kp.a8x2[l] * (d22 + dm22);
+    const C psl = sm.psi[l][cy][cx];
+    // Eq. alphaG (and the constant x acceleration)
+    Fx[l] = -kp.gx * rl * crx - psl * sx + rl * kp.body_fx;
+    Fy[l] = -kp.gx * rl * cry - psl * sy + rl * kp.alpha_g * T;
   }
+}
 
+// Reciprocals of rho_1, rho_2 and rho_1 + rho_2 from one division.
+template <class C> __device__ __forceinline__ void three_reciprocals(C r1, C r2, C& i1, C& i2, C& irho) {
+  const C rho = r1 + r2;
+  const C p12 = r1 * r2;
+  const C inv = recip<C>(p12 * rho);
+  i1 = r2 * rho * inv;
+  i2 = r1 * rho * inv;
+  irho = p12 * inv;
+}
+
+// BGK relaxation of the 27 populations of one node (Eqs. BGK, LBMg, Teq); in shifted storage the
+// deviations relax: f^eq - w_i rho_bar = w_i (drho + rho P_i(u)).  With tau = 1 (tau_g = 1) the
+// post-collision population is the equilibrium itself and the relaxation arithmetic is skipped.
+template <class C, bool SHIFT, bool RELAX>
+__device__ __forceinline__ void collide_fluid(const KParams<C>& kp, const C f[9], const C h[9], C r1, C r2, C dr1,
+                                              C dr2, C ux, C uy, C irl0, C irl1, const C Fx[2], const C Fy[2],
+                                              C post[27]) {
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    const C rl = (l == 0) ? r1 : r2;
+    const C inv_rl = (l == 0) ? irl0 : irl1;
+    const C ulx = ux + kp.tau * Fx[l] * inv_rl, uly = uy + kp.tau * Fy[l] * inv_rl;
+    const C usq = C(1.5) * (ulx * ulx + uly * uly);
+    const C base = SHIFT ? ((l == 0) ? dr1 : dr2) : rl;
+    const C* pop = (l == 0) ? f : h;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const C cu = C(cxq(i)) * ulx + C(cyq(i)) * uly;
+      const C poly = cu * (C(3) + C(4.5) * cu) - usq;
+      const C feq = wq<C>(i) * (base + rl * poly);
+      post[9 * l + i] = RELAX ? pop[i] + (feq - pop[i]) * kp.inv_tau : feq;
+    }
+  }
+}
+
+template <class C, bool SHIFT, bool RELAX>
+__device__ __forceinline__ void collide_thermal(const KParams<C>& kp, const C g[9], C T, C dT, C uHx, C uHy,
+                                                C post[27]) {
+  const C usq = C(1.5) * (uHx * uHx + uHy * uHy);
+  const C base = SHIFT ? dT : T;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const C cu = C(cxq(i)) * uHx + C(cyq(i)) * uHy;
+    const C poly = cu * (C(3) + C(4.5) * cu) - usq;
+    const C geq = wq<C>(i) * (base + T * poly);
+    post[18 + i] = RELAX ? g[i] + (geq - g[i]) * kp.inv_tau_g : geq;
+  }
+}
+
+template <class C, bool SHIFT>
+__device__ __forceinline__ void node_collide(const KParams<C>& kp, const C f[9], const C h[9], const C g[9], C r1, C r2,
+                                             C dr1, C dr2, C T, C dT, C ux, C uy, C irl0, C irl1, const C Fx[2],
+                                             const C Fy[2], C uHx, C uHy, C post[27]) {
+  if (kp.tau_is_one)
+    collide_fluid<C, SHIFT, false>(kp, f, h, r1, r2, dr1, dr2, ux, uy, irl0, irl1, Fx, Fy, post);
+  else
+    collide_fluid<C, SHIFT, true>(kp, f, h, r1, r2, dr1, dr2, ux, uy, irl0, irl1, Fx, Fy, post);
+  if (kp.tau_g_is_one)
+    collide_thermal<C, SHIFT, false>(kp, g, T, dT, uHx, uHy, post);
+  else
+    collide_thermal<C, SHIFT, true>(kp, g, T, dT, uHx, uHy, post);
+}
+
+// Phase B on one tile.  MODE_STEP: collide and push-store; MODE_OBS: accumulate the observables
+// of the node into acc[]; MODE_FIELDS: write rho1, rho2, T, u^(H) to aux planes.
+template <class S, class C, bool SHIFT, int MODE, bool FAST, int TX, int TY, int BY, bool CG>
+__device__ __forceinline__ void tile_phase_b(const S* __restrict__ fin, S* __restrict__ fout, const KParams<C>& kp,
+                                             int x0, int y0, const TileSmem<C, TX, TY, MODE != MODE_STEP>& sm,
+                                             double* __restrict__ aux, double acc[kObsSlots]) {
+  const int nx = kp.nx, ny = kp.ny, pitch = kp.pitch, plane = kp.plane;
+  const C Tb = SHIFT ? kp.T_bar : C(0);
 #pragma unroll 1
   for (int k = 0; k < TY / BY; ++k) {
     const int tx = threadIdx.x, ty = threadIdx.y + k * BY;
     const int gx = x0 + tx, gy = y0 + ty;
-    if (gx >= nx || gy >= ny) continue;
+    if (!FAST && (gx >= nx || gy >= ny)) continue;
     const int cx = tx + 2, cy = ty + 2;
-    if (s_solid[cy][cx]) {
-      if (MODE == MODE_FIELDS) {
+    if (!FAST && sm.solid[cy][cx]) {
+      if constexpr (MODE == MODE_FIELDS) {
         const long long n = (long long)gy * nx + gx, N = (long long)nx * ny;
-        aux[n] = cfg.rho_w[0];
-        aux[N + n] = cfg.rho_w[1];
-        aux[2 * N + n] = (2 * gy < ny) ? cfg.T_down : cfg.T_up;
+        aux[n] = kp.rho_w_d[0];
+        aux[N + n] = kp.rho_w_d[1];
+        aux[2 * N + n] = (2 * gy < ny) ? kp.T_down_d : kp.T_up_d;
         aux[3 * N + n] = 0.0;
         aux[4 * N + n] = 0.0;
       }
       continue;
     }
-    const long long idx = (long long)gy * pitch + gx;
+    const int idx = gy * pitch + gx;
+    const S* src = fin + idx;
+    // moments (Sec. 2.1, 2.3): densities and momentum from phase A, T from the thermal populations;
+    // in shifted storage the sums are deviations from the shift
     C f[9], h[9], g[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      f[i] = C(fin[i * plane + idx]);
-      h[i] = C(fin[(9 + i) * plane + idx]);
-      g[i] = C(fin[(18 + i) * plane + idx]);
-    }
-    // moments (Sec. 2.1, 2.3); in shifted storage the sums are deviations from the shift
-    const C r1 = s_rho[0][cy][cx], r2 = s_rho[1][cy][cx];
-    C dr1 = C(0), dr2 = C(0), dT = C(0);
+    for (int i = 0; i < 9; ++i) g[i] = C(ld_pop<CG>(src + (18 + i) * plane));
+    const bool relax = !kp.tau_is_one;
+    if (relax) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      dr1 += f[i];
-      dr2 += h[i];
-      dT += g[i];
+      for (int i = 0; i < 9; ++i) {
+        f[i] = C(ld_pop<CG>(src + i * plane));
+        h[i] = C(ld_pop<CG>(src + (9 + i) * plane));
+      }
     }
+    const C dr1 = sm.rho[0][cy][cx], dr2 = sm.rho[1][cy][cx];
+    const C r1 = SHIFT ? dr1 + kp.rho_bar[0] : dr1, r2 = SHIFT ? dr2 + kp.rho_bar[1] : dr2;
+    C dT = C(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) dT += g[i];
     const C T = dT + Tb;
-    const C jx = (f[1] - f[3] + f[5] - f[6] - f[7] + f[8]) + (h[1] - h[3] + h[5] - h[6] - h[7] + h[8]);
-    const C jy = (f[2] - f[4] + f[5] + f[6] - f[7] - f[8]) + (h[2] - h[4] + h[5] + h[6] - h[7] - h[8]);
-
-    // forces, Eqs. FAB, FintAttrattive, FintRepulsive, alphaG
+    const C jx = sm.jx[ty][tx], jy = sm.jy[ty][tx];
     C Fx[2], Fy[2];
-#pragma unroll
-    for (int l = 0; l < 2; ++l) {
-      const int m = 1 - l;
-      // cross term: -G12/rho0^2 rho_l(x) sum_{NN} w_i rho_m(x + c_i) c_i, as pair differences
-      const C e10 = s_rho[m][cy][cx + 1] - s_rho[m][cy][cx - 1];
-      const C e01 = s_rho[m][cy + 1][cx] - s_rho[m][cy - 1][cx];
-      const C e11 = s_rho[m][cy + 1][cx + 1] - s_rho[m][cy - 1][cx - 1];
-      const C em1 = s_rho[m][cy + 1][cx - 1] - s_rho[m][cy - 1][cx + 1];
-      const C w1 = C(1) / C(9), w2 = C(1) / C(36);
-      const C crx = w1 * e10 + w2 * (e11 - em1);
-      const C cry = w1 * e01 + w2 * (e11 + em1);
-      const C rl = (l == 0) ? r1 : r2;
-      // self term: -psi_l(x) sum_{24 links} (G^a_ll w_i + G^r_ll p_i) psi_l(x + c_i) c_i
-      const C d10 = s_psi[l][cy][cx + 1] - s_psi[l][cy][cx - 1];
-      const C d01 = s_psi[l][cy + 1][cx] - s_psi[l][cy - 1][cx];
-      const C d11 = s_psi[l][cy + 1][cx + 1] - s_psi[l][cy - 1][cx - 1];
-      const C dm1 = s_psi[l][cy + 1][cx - 1] - s_psi[l][cy - 1][cx + 1];
-      const C d20 = s_psi[l][cy][cx + 2] - s_psi[l][cy][cx - 2];
-      const C d02 = s_psi[l][cy + 2][cx] - s_psi[l][cy - 2][cx];
-      const C d12 = s_psi[l][cy + 2][cx + 1] - s_psi[l][cy - 2][cx - 1];
-      const C dm12 = s_psi[l][cy + 2][cx - 1] - s_psi[l][cy - 2][cx + 1];
-      const C d21 = s_psi[l][cy + 1][cx + 2] - s_psi[l][cy - 1][cx - 2];
-      const C dm21 = s_psi[l][cy + 1][cx - 2] - s_psi[l][cy - 1][cx + 2];
-      const C d22 = s_psi[l][cy + 2][cx + 2] - s_psi[l][cy - 2][cx - 2];
-      const C dm22 = s_psi[l][cy + 2][cx - 2] - s_psi[l][cy - 2][cx + 2];
-      const C a1 = C(cfg.a1[l]), a2 = C(cfg.a2[l]), a4 = C(cfg.a4x2[l]), a5 = C(cfg.a5[l]), a8 = C(cfg.a8x2[l]);
-      const C sx = a1 * d10 + a2 * (d11 - dm1) + a4 * d20 + a5 * (d12 - dm12 + C(2) * (d21 - dm21)) + a8 * (d22 - dm22);
-      const C sy = a1 * d01 + a2 * (d11 + dm1) + a4 * d02 + a5 * (C(2) * (d12 + dm12) + d21 + dm21) + a8 * (d22 + dm22);
-      const C psl = s_psi[l][cy][cx];
-      Fx[l] = -gxc * rl * crx - psl * sx + rl * bfx;
-      Fy[l] = -gxc * rl * cry - psl * sy + rl * ag * T;
-    }
-
+    node_forces<C, TX, TY, MODE != MODE_STEP>(sm, kp, cx, cy, r1, r2, T, Fx, Fy);
     // velocities: Eq. velo, Eq. shift, u^(H) = u + F / (2 rho)
+    C i1, i2, inv_rho;
+    three_reciprocals<C>(r1, r2, i1, i2, inv_rho);
     const C rho = r1 + r2;
-    const C inv_rho = C(1) / rho;
     const C ux = jx * inv_rho, uy = jy * inv_rho;
     const C uHx = ux + C(0.5) * (Fx[0] + Fx[1]) * inv_rho;
     const C uHy = uy + C(0.5) * (Fy[0] + Fy[1]) * inv_rho;
 
-    if (MODE == MODE_OBS) {
-      const C Tc = T;
-      const C Tup = s_solid[cy + 1][cx] ? C(2) * s_T[NEED_T ? cy + 1 : 0][NEED_T ? cx : 0] - Tc
-                                         : s_T[NEED_T ? cy + 1 : 0][NEED_T ? cx : 0];
-      const C Tdn = s_solid[cy - 1][cx] ? C(2) * s_T[NEED_T ? cy - 1 : 0][NEED_T ? cx : 0] - Tc
-                                         : s_T[NEED_T ? cy - 1 : 0][NEED_T ? cx : 0];
+    if constexpr (MODE == MODE_OBS) {
+      const C Tup = sm.solid[cy + 1][cx] ? C(2) * sm.T[cy + 1][cx] - T : sm.T[cy + 1][cx];
+      const C Tdn = sm.solid[cy - 1][cx] ? C(2) * sm.T[cy - 1][cx] - T : sm.T[cy - 1][cx];
       acc[0] += (double)dr1;
       acc[1] += (double)dr2;
       acc[2] += (double)(rho * uHx);
@@ -222,88 +379,94 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const StepCfg cf
                        !isfinite((double)T);
       acc[7] += bad ? 1.0 : 0.0;
       acc[8] += 1.0;
-      continue;
-    }
-    if (MODE == MODE_FIELDS) {
+    } else if constexpr (MODE == MODE_FIELDS) {
       const long long n = (long long)gy * nx + gx, N = (long long)nx * ny;
       aux[n] = (double)r1;
       aux[N + n] = (double)r2;
       aux[2 * N + n] = (double)T;
       aux[3 * N + n] = (double)uHx;
       aux[4 * N + n] = (double)uHy;
-      continue;
-    }
-
-    // BGK collisions: f* = f + (f^eq(rho_l, u_l) - f) / tau, g* = g + (g^eq(T, u^(H)) - g) / tau_g.
-    // Shifted storage relaxes the deviations: f^eq - w_i rho_bar = w_i (drho + rho P_i(u)).
-    C post[27];
+    } else {
+      C post[27];
+      node_collide<C, SHIFT>(kp, f, h, g, r1, r2, dr1, dr2, T, dT, ux, uy, i1, i2, Fx, Fy, uHx, uHy, post);
+      // streaming (push) with half-way bounce-back / thermal anti-bounce-back
+      if constexpr (FAST) {
+        S* dst = fout + idx;
 #pragma unroll
-    for (int l = 0; l < 2; ++l) {
-      const C rl = (l == 0) ? r1 : r2;
-      const C inv_rl = C(1) / rl;
-      const C ulx = ux + tau * Fx[l] * inv_rl, uly = uy + tau * Fy[l] * inv_rl;
-      const C usq = C(1.5) * (ulx * ulx + uly * uly);
-      const C base = SHIFT ? ((l == 0) ? dr1 : dr2) : rl;
-      const C* pop = (l == 0) ? f : h;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const C cu = C(cxq(i)) * ulx + C(cyq(i)) * uly;
-        const C poly = cu * (C(3) + C(4.5) * cu) - usq;
-        const C feq = wq<C>(i) * (base + rl * poly);
-        post[9 * l + i] = pop[i] + (feq - pop[i]) * inv_tau;
-      }
-    }
-    {
-      const C usq = C(1.5) * (uHx * uHx + uHy * uHy);
-      const C base = SHIFT ? dT : T;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const C cu = C(cxq(i)) * uHx + C(cyq(i)) * uHy;
-        const C poly = cu * (C(3) + C(4.5) * cu) - usq;
-        const C geq = wq<C>(i) * (base + T * poly);
-        post[18 + i] = g[i] + (geq - g[i]) * inv_tau_g;
-      }
-    }
-
-    // streaming (push) with half-way bounce-back / thermal anti-bounce-back
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const int sxl = cx + cxq(i), syl = cy + cyq(i);
-      if (!s_solid[syl][sxl]) {
-        int dx = gx + cxq(i);
-        dx = dx < 0 ? dx + nx : (dx >= nx ? dx - nx : dx);
-        int dy = gy + cyq(i);
-        if (cfg.periodic_y) dy = dy < 0 ? dy + ny : (dy >= ny ? dy - ny : dy);
-        const long long didx = (long long)dy * pitch + dx;
-        fout[i * plane + didx] = S(post[i]);
-        fout[(9 + i) * plane + didx] = S(post[9 + i]);
-        fout[(18 + i) * plane + didx] = S(post[18 + i]);
+        for (int i = 0; i < 9; ++i) {
+          const int off = cxq(i) + cyq(i) * pitch;
+          dst[i * plane + off] = S(post[i]);
+          dst[(9 + i) * plane + off] = S(post[9 + i]);
+          dst[(18 + i) * plane + off] = S(post[18 + i]);
+        }
       } else {
-        const int o = oppq(i);
-        const int wy = gy + cyq(i);
-        const C Tw = C(2 * wy < ny ? cfg.T_down : cfg.T_up) - Tb;
-        fout[o * plane + idx] = S(post[i]);
-        fout[(9 + o) * plane + idx] = S(post[9 + i]);
-        fout[(18 + o) * plane + idx] = S(-post[18 + i] + C(2) * wq<C>(i) * Tw);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          if (!sm.solid[cy + cyq(i)][cx + cxq(i)]) {
+            int dx = gx + cxq(i);
+            dx = dx < 0 ? dx + nx : (dx >= nx ? dx - nx : dx);
+            int dy = gy + cyq(i);
+            if (kp.periodic_y) dy = dy < 0 ? dy + ny : (dy >= ny ? dy - ny : dy);
+            const int didx = dy * pitch + dx;
+            fout[i * plane + didx] = S(post[i]);
+            fout[(9 + i) * plane + didx] = S(post[9 + i]);
+            fout[(18 + i) * plane + didx] = S(post[18 + i]);
+          } else {
+            const int o = oppq(i);
+            const C twoTw = (2 * (gy + cyq(i)) < ny) ? kp.twoTw_down : kp.twoTw_up;
+            fout[o * plane + idx] = S(post[i]);
+            fout[(9 + o) * plane + idx] = S(post[9 + i]);
+            fout[(18 + o) * plane + idx] = S(-post[18 + i] + wq<C>(i) * twoTw);
+          }
+        }
       }
     }
   }
+}
 
-  if (MODE == MODE_OBS) {
-    __shared__ double s_red[NT / 32][kObsSlots];
-    const int lane = tid & 31, warp = tid >> 5;
+// One tile: phase A, barrier, phase B (fast path when the CTA allows it).
+template <class S, class C, bool SHIFT, int MODE, int TX, int TY, int BY, bool CG = false>
+__device__ __forceinline__ void tile_step(const S* __restrict__ fin, S* __restrict__ fout, const KParams<C>& kp,
+                                          int x0, int y0, TileSmem<C, TX, TY, MODE != MODE_STEP>& sm,
+                                          double* __restrict__ aux, double acc[kObsSlots]) {
+  constexpr int NT = TX * BY;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  const bool fast = tile_phase_a<S, C, SHIFT, MODE != MODE_STEP, TX, TY, NT, CG>(fin, kp, x0, y0, sm, tid);
+  if (MODE == MODE_STEP && fast)
+    tile_phase_b<S, C, SHIFT, MODE, true, TX, TY, BY, CG>(fin, fout, kp, x0, y0, sm, aux, acc);
+  else
+    tile_phase_b<S, C, SHIFT, MODE, false, TX, TY, BY, CG>(fin, fout, kp, x0, y0, sm, aux, acc);
+}
+
+// Block-wide deterministic sum of the observable accumulators into aux[slot * kObsSlots + v].
+template <int NT>
+__device__ __forceinline__ void block_obs_store(double acc[kObsSlots], double* __restrict__ aux, long long slot) {
+  __shared__ double s_red[NT / 32][kObsSlots];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
-    for (int v = 0; v < kObsSlots; ++v) {
-      const double s = warp_sum(acc[v]);
-      if (lane == 0) s_red[warp][v] = s;
-    }
-    __syncthreads();
-    if (tid < kObsSlots) {
-      double s = 0.0;
-      for (int w = 0; w < NT / 32; ++w) s += s_red[w][tid];
-      aux[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * kObsSlots + tid] = s;
-    }
+  for (int v = 0; v < kObsSlots; ++v) {
+    const double s = warp_sum(acc[v]);
+    if (lane == 0) s_red[warp][v] = s;
   }
+  __syncthreads();
+  if (tid < kObsSlots) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += s_red[w][tid];
+    aux[slot * kObsSlots + tid] = s;
+  }
+}
+
+template <class S, class C, bool SHIFT, int MODE, int TX, int TY, int BY, int MINB>
+__global__ void __launch_bounds__(TX * BY, MINB)
+lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const KParams<C> kp, double* __restrict__ aux) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& sm = *reinterpret_cast<TileSmem<C, TX, TY, MODE != MODE_STEP>*>(smem_raw);
+  double acc[kObsSlots];
+#pragma unroll
+  for (int v = 0; v < kObsSlots; ++v) acc[v] = 0.0;
+  tile_step<S, C, SHIFT, MODE, TX, TY, BY>(fin, fout, kp, blockIdx.x * TX, blockIdx.y * TY, sm, aux, acc);
+  if constexpr (MODE == MODE_OBS) block_obs_store<TX * BY>(acc, aux, (long long)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // Rest equilibria f = w_i rho, g = w_i T at fluid nodes (stored minus the shift), 0 at solid nodes.
@@ -358,26 +521,55 @@ __global__ void lb_plane_put_kernel(int k, const double* __restrict__ in, S* __r
   buf[k * cfg.plane + (long long)gy * cfg.pitch + gx] = solid ? S(0) : S(v);
 }
 
+// Launch with the tile's shared memory as dynamic shared memory (the larger tiles need more than
+// the 48 KB static limit); the opt-in attribute is set once per kernel instantiation.
+template <class S, int MODE, int TX, int TY, int BY, int MB, bool SHIFT>
+cudaError_t launch_tile_kernel(const dim3& grid, const S* in, S* out, const KParams<S>& kp, double* aux,
+                               cudaStream_t s) {
+  constexpr size_t bytes = sizeof(TileSmem<S, TX, TY, MODE != MODE_STEP>);
+  auto kern = lb_step_kernel<S, S, SHIFT, MODE, TX, TY, BY, MB>;
+  static std::atomic<unsigned long long> done{0};  // one bit per device ordinal (mod 64)
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(done.load() & bit)) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    done.fetch_or(bit);
+  }
+  kern<<<grid, dim3(TX, BY, 1), bytes, s>>>(in, out, kp, aux);
+  return cudaGetLastError();
+}
+
+template <class S> struct MinBlocks;
+template <> struct MinBlocks<double> { static constexpr int value = 2; };
+template <> struct MinBlocks<float> { static constexpr int value = 3; };
+
 template <class S, bool SHIFT>
 cudaError_t launch_impl(int mode, const StepCfg& c, const void* fin, void* fout, double* aux, cudaStream_t s) {
   using T = Tile<S>;
-  const dim3 grid = grid_for(c.nx, c.ny, T::TX, T::TY), block(T::TX, T::BY, 1);
+  constexpr int MB = MinBlocks<S>::value;
+  const dim3 grid = grid_for(c.nx, c.ny, T::TX, T::TY);
   const S* in = static_cast<const S*>(fin);
   S* out = static_cast<S*>(fout);
+  const KParams<S> kp = make_kparams<S>(c);
   switch (mode) {
     case MODE_STEP:
-      lb_step_kernel<S, S, SHIFT, MODE_STEP, T::TX, T::TY, T::BY><<<grid, block, 0, s>>>(in, out, c, aux);
-      break;
+      return launch_tile_kernel<S, MODE_STEP, T::TX, T::TY, T::BY, MB, SHIFT>(grid, in, out, kp, aux, s);
     case MODE_OBS:
-      lb_step_kernel<S, S, SHIFT, MODE_OBS, T::TX, T::TY, T::BY><<<grid, block, 0, s>>>(in, out, c, aux);
-      break;
+      return launch_tile_kernel<S, MODE_OBS, T::TX, T::TY, T::BY, 1, SHIFT>(grid, in, out, kp, aux, s);
     case MODE_FIELDS:
-      lb_step_kernel<S, S, SHIFT, MODE_FIELDS, T::TX, T::TY, T::BY><<<grid, block, 0, s>>>(in, out, c, aux);
-      break;
+      return launch_tile_kernel<S, MODE_FIELDS, T::TX, T::TY, T::BY, 1, SHIFT>(grid, in, out, kp, aux, s);
     default:
       return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+}
+
+template <class S, bool SHIFT, int TX, int TY, int BY, int MB>
+cudaError_t launch_step_shape(const StepCfg& c, const void* fin, void* fout, cudaStream_t s) {
+  return launch_tile_kernel<S, MODE_STEP, TX, TY, BY, MB, SHIFT>(grid_for(c.nx, c.ny, TX, TY), static_cast<const S*>(fin),
+                                                               static_cast<S*>(fout), make_kparams<S>(c), nullptr, s);
 }
 
 inline dim3 rows_grid(const StepCfg& c) { return dim3((unsigned)((c.nx + 127) / 128), (unsigned)c.ny, 1u); }

@@ -20,7 +20,8 @@ _NAMES = {0: "LB_OK", -1: "LB_EINVAL", -2: "LB_ENOSPACE", -3: "LB_ECUDA", -4: "L
 
 # every symbol include/tlb.h declares
 EXPORTS = ("lb_workspace_size", "lb_init", "lb_step", "lb_observables", "lb_get_fields", "lb_get_state",
-           "lb_set_state", "lb_sync", "lb_destroy", "lb_last_error", "lb_version")
+           "lb_set_state", "lb_sync", "lb_destroy", "lb_last_error", "lb_version", "lb_autotune", "lb_set_tile",
+           "lb_tile_info")
 
 
 class LbError(RuntimeError):
@@ -71,10 +72,13 @@ def lib():
         L.lb_destroy.restype = None
         L.lb_last_error.argtypes = [vp]
         L.lb_last_error.restype = ctypes.c_char_p
+        L.lb_autotune.argtypes = [vp, i, ctypes.POINTER(i), dp, i]
+        L.lb_set_tile.argtypes = [vp, i]
+        L.lb_tile_info.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
         L.lb_version.argtypes = []
         L.lb_version.restype = ctypes.c_char_p
         for f in ("lb_workspace_size", "lb_init", "lb_step", "lb_observables", "lb_get_fields", "lb_get_state",
-                  "lb_set_state", "lb_sync"):
+                  "lb_set_state", "lb_sync", "lb_autotune", "lb_set_tile", "lb_tile_info"):
             getattr(L, f).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -167,6 +171,24 @@ class Lattice:
         if st.shape != (27, self.ny, self.nx):
             raise ValueError("state must have shape (27, ny, nx)")
         _check(lib().lb_set_state(self._h, _dp(st), st.nbytes), self._h)
+
+    def tile_info(self, candidate=-1):
+        tx, ty, th = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        n = lib().lb_tile_info(self._h, int(candidate), ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(th))
+        if n < 0:
+            _check(n, self._h)
+        return {"tx": tx.value, "ty": ty.value, "threads": th.value, "candidates": n}
+
+    def autotune(self, launches=20):
+        """Time every tile candidate (state unchanged) and keep the fastest; returns (index, ms list)."""
+        n = self.tile_info(0)["candidates"]
+        ms = np.zeros(n)
+        chosen = ctypes.c_int()
+        _check(lib().lb_autotune(self._h, int(launches), ctypes.byref(chosen), _dp(ms), n), self._h)
+        return chosen.value, ms.tolist()
+
+    def set_tile(self, candidate):
+        _check(lib().lb_set_tile(self._h, int(candidate)), self._h)
 
     def sync(self):
         _check(lib().lb_sync(self._h), self._h)

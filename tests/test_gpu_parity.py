@@ -171,6 +171,7 @@ def test_full_size_1024x512_against_oracle(precision, steps, tol):
     against the oracle on every node (the OpenMP oracle finishes this in seconds)."""
     w = I.emulsion_1024x512()
     g, o = _pair(w.params, w.rho1, w.rho2, w.T0, precision=precision, omp=True)
+    g.autotune(launches=3)  # the benchmark times the autotuned tile
     g.step(steps)
     o.step(steps)
     fg, fo = g.fields(), o.fields()
@@ -220,3 +221,52 @@ def test_init_errors():
     with pytest.raises(lb.LbError) as e:
         lb.Lattice(w.params, bad, w.rho2, w.T0)
     assert e.value.code == lb.LB_EINVAL
+
+
+@pytest.mark.parametrize("precision", [lb.LB_FP64, lb.LB_FP32_SHIFTED])
+@pytest.mark.parametrize("periodic", [0, 1])
+def test_every_tile_candidate_gives_identical_results(precision, periodic):
+    """Tile shapes only change which CTA computes a node, never the arithmetic of a node: every
+    autotuner candidate must give bit-identical populations (fast interior path and general path)."""
+    nx, ny = 300, 130
+    if periodic:
+        y, x = np.mgrid[0:ny, 0:nx]
+        r1 = np.where(((x - 150) ** 2 + (y - 60) ** 2) < 30 ** 2, 1.4, 0.1)
+        params = dict(I.EMULSION_PARAMS, nx=nx, ny=ny, periodic_y=1, T_down=0.0, T_up=0.0, alpha_g=1e-4)
+        T0 = 0.1 * np.sin(2 * np.pi * x / nx)
+        mask = None
+    else:
+        w = I.emulsion_hex(nx, ny, 6, 3, 0.7, 3e4, seed=9)
+        params, r1, T0 = w.params, w.rho1, w.T0
+        mask = I.posts_mask(nx, ny, 4, 5, 25)
+    ref = None
+    n_cand = None
+    for k in range(16):
+        g = lb.Lattice(params, r1, 1.5 - r1, T0, mask=mask, precision=precision)
+        n_cand = g.tile_info(0)["candidates"]
+        if k >= n_cand:
+            break
+        g.set_tile(k)
+        g.step(21)
+        st = g.get_state()
+        if ref is None:
+            ref = st
+        else:
+            np.testing.assert_array_equal(st, ref, err_msg=f"candidate {k}")
+    assert n_cand >= 2
+
+
+def test_autotune_keeps_state_and_picks_a_candidate():
+    w = I.emulsion_small()
+    g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, precision=lb.LB_FP32_SHIFTED)
+    g.step(3)
+    before = g.get_state()
+    k, ms = g.autotune(launches=3)
+    assert 0 <= k < len(ms) and all(m > 0 for m in ms)
+    assert ms[k] == min(ms)
+    np.testing.assert_array_equal(g.get_state(), before)
+    assert g.observables()["step"] == 3
+    g.step(5)
+    h = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, precision=lb.LB_FP32_SHIFTED)
+    h.step(8)
+    np.testing.assert_array_equal(g.get_state(), h.get_state())
