@@ -168,6 +168,34 @@ def time_form(w, precision, steps, warmup, flush, tile=-1):
                      "autotune_ms_per_candidate": [round(m, 5) for m in cand_ms]}}
 
 
+def time_batch(reps, steps, warmup, trial_steps=16):
+    """The ensemble in one lb_batch: autotune (schedule x tile; those steps are real steps), W warm-up
+    steps, then K steps timed with CUDA events on the batch's stream (inputs >> L2, no flush)."""
+    import torch
+
+    from paper_2109_12565_gb300 import lb
+
+    b = lb.Batch([w.params for w in reps], [w.rho1 for w in reps], [w.rho2 for w in reps], [w.T0 for w in reps],
+                 masks=[w.mask for w in reps], precision=lb.LB_FP32_SHIFTED)
+    tune = b.autotune(trial_steps=trial_steps)
+    b.step(warmup)
+    assert b.sync() == 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.step(steps)
+    e1.record(b.stream)
+    torch.cuda.synchronize()
+    rc = b.sync()
+    ms = e0.elapsed_time(e1)
+    nodes = sum(w.params["nx"] * w.params["ny"] for w in reps)
+    info = b.info()
+    obs0 = b.observables(0)
+    b.close()
+    assert rc == 0
+    return {"ms_total": ms, "ms_per_step": ms / steps, "nodes": nodes, "info": info, "tune": tune,
+            "Nu_replica0": obs0["Nu"]}
+
+
 def time_e2e(w, precision, steps, obs_every=500):
     """End to end through the C ABI: lb_init from pinned host fields, `steps` steps (graph replays),
     observables every `obs_every` steps and at the end, fields back to pinned host memory."""
@@ -264,9 +292,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="fp32,fp64", help="comma list of fp32, fp64 (profiling runs)")
+    ap.add_argument("--forms", default="fp32,fp64,batched", help="comma list of fp32, fp64, batched")
     ap.add_argument("--fp64-steps", type=int, default=0, help="timed FP64 steps (default steps // 4)")
     ap.add_argument("--tile", type=int, default=-1, help="fixed tile candidate instead of autotuning")
+    ap.add_argument("--batch-steps", type=int, default=200, help="timed steps of the 64-replica ensemble")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -296,6 +325,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     forms_req = set(args.forms.split(","))
+    ens = I.ensemble() if "batched" in forms_req else None
     steps64 = args.fp64_steps or max(3, args.steps // 4)
     r32 = r64 = None
     with ClockSampler(local) as clk:
@@ -303,6 +333,7 @@ def main():
             r32 = time_form(w, lb.LB_FP32_SHIFTED, args.steps, args.warmup, flush, args.tile)
         if "fp64" in forms_req:
             r64 = time_form(w, lb.LB_FP64, steps64, args.warmup, flush, args.tile)
+        rb = time_batch(ens, args.batch_steps, args.warmup) if ens else None
     torch.cuda.synchronize()
     t32 = r32["ms_total"] if r32 else 0.0
     t64 = r64["ms_total"] if r64 else 0.0
@@ -346,6 +377,20 @@ def main():
             forms["fp64"]["alu_frac_of_nominal"] = forms["fp64"]["dp_tflops"] / FP64_NOMINAL_TFLOPS
     if r32 and r64:
         forms["fp32_over_fp64"] = mlups32 / mlups64
+    if rb:
+        tb = rb["ms_total"]
+        if dist:
+            t = torch.tensor([tb], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tb = float(t[0])
+        achb = 216.0 * rb["nodes"] / (rb["ms_per_step"] * 1e-3) / 1e9
+        forms["batched"] = {"MLUPS": world * rb["nodes"] * args.batch_steps / (tb * 1e3), "replicas": len(ens),
+                            "nodes": rb["nodes"], "ms_per_step": rb["ms_per_step"], "hbm_frac": achb / peak,
+                            "GBps": achb, "schedule": ["per-step graph", "persistent"][rb["info"]["schedule"]],
+                            "tile_candidate": rb["info"]["tile"], "work_items": rb["info"]["items"],
+                            "persistent_grid": rb["info"]["grid"], "graphs": rb["info"]["graphs"],
+                            "autotune_ms_per_step": rb["tune"]["ms_per_step"], "steps": args.batch_steps,
+                            "Nu_replica0": rb["Nu_replica0"]}
     head = r32 or r64
     line = {
         "metric": METRIC, "value": mlups32 if r32 else mlups64, "unit": "MLUPS", "n_gpus": world,
@@ -359,7 +404,8 @@ def main():
         "roofline": roof,
         "forms": forms,
         "e2e": e2e,
-        "gpu_launches": (args.steps if r32 else 0) + (steps64 if r64 else 0),
+        "gpu_launches": (args.steps if r32 else 0) + (steps64 if r64 else 0) + (
+            (args.batch_steps if rb["info"]["schedule"] == 0 else -(-args.batch_steps // 64)) if rb else 0),
         "clocks": clk.summary(),
     }
     if not args.no_cpu_baseline:

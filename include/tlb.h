@@ -162,6 +162,61 @@ int lb_tile_info(const lb_handle* h, int candidate, int* tx, int* ty, int* threa
 int lb_observables_static(const lb_params* p, const double* d_state, const uint8_t* d_mask, lb_obs* out,
                           void* stream);
 
+/* ---- Batched ensembles (not in the paper): n independent lattices, each with its own lb_params
+ * (size, couplings, Rayleigh number, precision equal for all), obstacle mask and state, advanced
+ * together by one launch per step or by one persistent launch per K steps.  Every replica runs the
+ * same fused step as lb_step; results are bit-identical to n separate handles. */
+typedef struct lb_batch lb_batch;
+
+/* Device workspace bytes for n replicas; has_mask[r] != 0 when replica r has a mask (may be NULL). */
+int lb_batch_workspace_size(const lb_params* reps, int n, const int* has_mask, size_t* bytes);
+
+/* Create a batch.  masks[r] (host nx*ny bytes, or NULL; masks itself may be NULL), rho1[r],
+ * rho2[r], T0[r] (host nx*ny doubles): as in lb_init for each replica.  d_workspace: caller-owned,
+ * 256-byte aligned, >= lb_batch_workspace_size.  Starts with schedule 0 and tile candidate 0.
+ * Synchronous. */
+int lb_batch_init(lb_batch** b, const lb_params* reps, int n, const uint8_t* const* masks, const double* const* rho1,
+                  const double* const* rho2, const double* const* T0, void* d_workspace, size_t ws_bytes, void* stream);
+
+/* Advance every replica by n >= 0 steps, asynchronously.  Schedule 0: CUDA-graph replay of one
+ * launch per step over all (replica, tile) items.  Schedule 1: cooperative persistent launches of
+ * steps_per_launch steps each (graph-captured when the driver allows it), with bounded waits on
+ * neighbour-tile step counters; a wait that runs out is reported as LB_ETIMEOUT by the next
+ * lb_batch_sync / lb_batch_observables / lb_batch_get_*, and the state is then invalid. */
+int lb_batch_step(lb_batch* b, int n);
+
+/* Choose the schedule (0 per-step, 1 persistent), the tile candidate and the steps per persistent
+ * launch (even, >= 2). */
+int lb_batch_configure(lb_batch* b, int schedule, int tile, int steps_per_launch);
+
+/* Autotuner: runs every (schedule, tile) pair for 2 * trial_steps real steps (the state advances;
+ * steps_taken receives the total), times the second half with CUDA events and keeps the fastest.
+ * ms (may be NULL) receives the milliseconds per step of pair (schedule s, tile t) at s * ntiles + t
+ * (n_slots >= 2 * ntiles). */
+int lb_batch_autotune(lb_batch* b, int trial_steps, int* schedule, int* tile, long long* steps_taken, double* ms,
+                      int n_slots);
+
+/* Current work-list size, persistent grid, schedule, tile and whether graphs are in use; returns the
+ * number of tile candidates. */
+int lb_batch_info(const lb_batch* b, int* n_items, int* grid, int* schedule, int* tile, int* graphs);
+
+/* Per-replica observables, fields and state, as lb_observables / lb_get_fields / lb_get_state. */
+int lb_batch_observables(lb_batch* b, int replica, lb_obs* out);
+int lb_batch_get_fields(lb_batch* b, int replica, double* rho1, double* rho2, double* T, double* ux, double* uy);
+int lb_batch_get_state(lb_batch* b, int replica, double* host, size_t bytes);
+
+/* Wait for the batch's stream; LB_ETIMEOUT if a persistent wait ran out. */
+int lb_batch_sync(lb_batch* b);
+
+/* Test hook for failure detection: sets the SM-clock budget of every persistent wait (default 4e9
+ * cycles, about 2 s) and, when withhold_item >= 0, makes the persistent kernel never publish that
+ * work item's step counter, so its neighbours' bounded waits run out and the launch ends with
+ * LB_ETIMEOUT instead of hanging. */
+int lb_batch_set_wait_budget(lb_batch* b, long long cycles, int withhold_item);
+
+void lb_batch_destroy(lb_batch* b);
+const char* lb_batch_last_error(const lb_batch* b);
+
 /* Wait for all work of the handle and report any asynchronous CUDA error. */
 int lb_sync(lb_handle* h);
 

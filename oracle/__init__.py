@@ -57,8 +57,10 @@ def lib(omp=False):
         L.orc_run.argtypes = [P, u8, dp, dp, ctypes.c_long]
         L.orc_fields.argtypes = [P, u8, dp, dp, dp, dp, dp, dp]
         L.orc_observables.argtypes = [P, u8, dp, dp]
+        L.orc_adjoint_step.argtypes = [P, u8, dp, dp, ctypes.c_double, dp, dp]
+        L.orc_adjoint_run.argtypes = [P, u8, dp, dp, dp, ctypes.c_long, dp, dp, dp]
         for f in ("orc_solid_map", "orc_init", "orc_forces", "orc_step", "orc_run", "orc_fields",
-                  "orc_observables"):
+                  "orc_observables", "orc_adjoint_step", "orc_adjoint_run"):
             getattr(L, f).restype = ctypes.c_int
         _LIBS[key] = L
     return _LIBS[key]
@@ -181,3 +183,32 @@ def available_cores():
         return len(os.sched_getaffinity(0))
     except AttributeError:  # pragma: no cover
         return os.cpu_count() or 1
+
+
+def adjoint_step(params, state, lam_out, cJ, mask=None):
+    """(lam_in, dJ/dT_down increment) of one reverse step at state S_t (see orc_adjoint_step)."""
+    cp = make_params(params)
+    st = np.ascontiguousarray(state, dtype=np.float64)
+    lo = None if lam_out is None else np.ascontiguousarray(lam_out, dtype=np.float64)
+    lam_in = np.zeros_like(st)
+    d = ctypes.c_double(0.0)
+    m, mp = _mask(mask)
+    _check(lib().orc_adjoint_step(ctypes.byref(cp), mp, _dp(st), None if lo is None else _dp(lo), float(cJ),
+                                  _dp(lam_in), ctypes.byref(d)), "adjoint_step")
+    return lam_in, d.value
+
+
+def adjoint_run(params, rho1, rho2, T0, nsteps, mask=None):
+    """(J, dJ/dT0 [ny, nx], dJ/dT_down) for J = time-averaged Nu over nsteps steps."""
+    cp = make_params(params)
+    ny, nx = int(params["ny"]), int(params["nx"])
+    r1 = np.ascontiguousarray(np.broadcast_to(rho1, (ny, nx)), dtype=np.float64)
+    r2 = np.ascontiguousarray(np.broadcast_to(rho2, (ny, nx)), dtype=np.float64)
+    t0 = np.ascontiguousarray(np.broadcast_to(T0, (ny, nx)), dtype=np.float64)
+    J = ctypes.c_double()
+    dT0 = np.zeros((ny, nx))
+    dTd = ctypes.c_double()
+    m, mp = _mask(mask)
+    _check(lib().orc_adjoint_run(ctypes.byref(cp), mp, _dp(r1), _dp(r2), _dp(t0), int(nsteps), ctypes.byref(J),
+                                 _dp(dT0), ctypes.byref(dTd)), "adjoint_run")
+    return J.value, dT0, dTd.value

@@ -429,3 +429,352 @@ int orc_observables(const orc_params* prm, const uint8_t* mask, const double* st
   free(solid);
   return 0;
 }
+
+/* ======================================================================================
+ * Discrete adjoint (reverse mode) of the step and of the time-averaged Nusselt number
+ * J = (1/N) sum_{t=1..N} Nu(S_t)  (Eq. NuTime), w.r.t. the initial temperature field and T_down.
+ *
+ * One reverse step maps lam_out = dJ/dS_{t+1} to lam_in = (dS_{t+1}/dS_t)^T lam_out + cJ dNu/dS_t,
+ * following the forward step of orc_step backwards, one sweep per forward sub-step:
+ *   streaming (+ bounce-back, anti-bounce-back) -> BGK collisions -> velocities (Eq. shift,
+ *   u^(H)) -> forces (Eqs. FAB, FintAttrattive, FintRepulsive, alphaG) -> pseudo-potentials ->
+ *   moments.  Solid and out-of-domain positions carry constants and receive no adjoint.
+ * ====================================================================================== */
+
+typedef struct {
+  uint8_t* solid;
+  double *rho1, *rho2, *jx, *jy, *T;
+  double *psit[2], *psie[2];
+  double *Fx[2], *Fy[2];
+} orc_fwd;
+
+static void fwd_free(orc_fwd* w) {
+  free(w->solid);
+  free(w->rho1);
+  free(w->rho2);
+  free(w->jx);
+  free(w->jy);
+  free(w->T);
+  for (int l = 0; l < 2; ++l) {
+    free(w->psit[l]);
+    free(w->psie[l]);
+    free(w->Fx[l]);
+    free(w->Fy[l]);
+  }
+}
+
+/* Forward intermediates of state S (moments, pseudo-potentials, forces per component). */
+static void fwd_recompute(const orc_params* prm, const uint8_t* mask, const double* S, orc_fwd* w) {
+  const long N = (long)prm->nx * prm->ny;
+  w->solid = (uint8_t*)malloc((size_t)N);
+  orc_solid_map(prm, mask, w->solid);
+  w->rho1 = (double*)malloc(sizeof(double) * N);
+  w->rho2 = (double*)malloc(sizeof(double) * N);
+  w->jx = (double*)malloc(sizeof(double) * N);
+  w->jy = (double*)malloc(sizeof(double) * N);
+  w->T = (double*)malloc(sizeof(double) * N);
+  moments(prm, w->solid, S, w->rho1, w->rho2, w->jx, w->jy, w->T);
+  double* F = (double*)malloc(sizeof(double) * 4 * N);
+  forces_from_fields(prm, w->solid, w->rho1, w->rho2, w->T, F);
+  const double* rho[2] = {w->rho1, w->rho2};
+  for (int l = 0; l < 2; ++l) {
+    w->psit[l] = (double*)malloc(sizeof(double) * N);
+    w->psie[l] = (double*)malloc(sizeof(double) * N);
+    w->Fx[l] = (double*)malloc(sizeof(double) * N);
+    w->Fy[l] = (double*)malloc(sizeof(double) * N);
+    for (long n = 0; n < N; ++n) {
+      w->psit[l][n] = w->solid[n] ? 0.0 : rho[l][n] / prm->rho0;
+      w->psie[l][n] = w->solid[n] ? 0.0 : psi_exp(rho[l][n], prm->rho0);
+      w->Fx[l][n] = F[((long)l * 2 + 0) * N + n];
+      w->Fy[l][n] = F[((long)l * 2 + 1) * N + n];
+    }
+  }
+  free(F);
+}
+
+/* Position (x, y) + c_k as a fluid node index, or -1 when it is solid or outside the domain. */
+static long fluid_at(const orc_params* prm, const uint8_t* solid, int x, int y) {
+  const int nx = prm->nx, ny = prm->ny;
+  x = wrap(x, nx);
+  if (prm->periodic_y)
+    y = wrap(y, ny);
+  else if (y < 0 || y >= ny)
+    return -1;
+  const long n = (long)y * nx + x;
+  return solid[n] ? -1 : n;
+}
+
+/* d(sum_z dT/dy(z))/dT_down for the mirror rule of the Nu discretisation (geometry only). */
+static double dB_dTdown_sum(const orc_params* prm, const uint8_t* solid) {
+  const int nx = prm->nx, ny = prm->ny;
+  double s = 0.0;
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      if (solid[(long)y * nx + x]) continue;
+      for (int sgn = -1; sgn <= 1; sgn += 2) {
+        int yy = y + sgn;
+        if (prm->periodic_y) yy = wrap(yy, ny);
+        if (solid[(long)yy * nx + x] && 2 * yy < ny) s += (double)sgn; /* d(T_up - T_dn)/2 / dT_w */
+      }
+    }
+  return s;
+}
+
+int orc_adjoint_step(const orc_params* prm, const uint8_t* mask, const double* S, const double* lam_out, double cJ,
+                     double* lam_in, double* dJ_dTdown) {
+  if (!valid(prm)) return -1;
+  const int nx = prm->nx, ny = prm->ny;
+  const long N = (long)nx * ny;
+  orc_fwd w;
+  fwd_recompute(prm, mask, S, &w);
+  const double tau = prm->tau, om = 1.0 / prm->tau, omg = 1.0 / prm->tau_g, rho0 = prm->rho0;
+  double dTd = 0.0;
+
+  /* Nusselt-number normalisation (Eq. NuTime) */
+  double nf = 0.0;
+  for (long n = 0; n < N; ++n) nf += w.solid[n] ? 0.0 : 1.0;
+  const double kappa = (prm->tau_g - 0.5) / 3.0, dT = prm->T_down - prm->T_up, H = (double)(ny - 2);
+  const int nu_defined = !prm->periodic_y && dT != 0.0 && nf > 0;
+  const double D = kappa * dT / H;
+
+  /* 1. reverse streaming: lam_star = adjoint of the post-collision populations */
+  double* lam_star = (double*)calloc(27 * (size_t)N, sizeof(double));
+  if (lam_out) {
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const long n = (long)y * nx + x;
+        if (w.solid[n]) continue;
+        for (int i = 0; i < 9; ++i) {
+          int xd = wrap(x + CX[i], nx), yd = y + CY[i];
+          if (prm->periodic_y) yd = wrap(yd, ny);
+          const long nd = (long)yd * nx + xd;
+          if (!w.solid[nd]) {
+            for (int c = 0; c < 3; ++c) lam_star[(long)(9 * c + i) * N + n] = lam_out[(long)(9 * c + i) * N + nd];
+          } else {
+            const int o = OPP[i];
+            lam_star[(long)i * N + n] = lam_out[(long)o * N + n];
+            lam_star[(long)(9 + i) * N + n] = lam_out[(long)(9 + o) * N + n];
+            lam_star[(long)(18 + i) * N + n] = -lam_out[(long)(18 + o) * N + n];
+            if (2 * yd < ny) dTd += 2.0 * weight_w(i) * lam_out[(long)(18 + o) * N + n];
+          }
+        }
+      }
+  }
+
+  /* 2. collision and velocity adjoints, local to each fluid node */
+  double* lFx[2];
+  double* lFy[2];
+  double* lrho[2];
+  for (int l = 0; l < 2; ++l) {
+    lFx[l] = (double*)calloc((size_t)N, sizeof(double));
+    lFy[l] = (double*)calloc((size_t)N, sizeof(double));
+    lrho[l] = (double*)calloc((size_t)N, sizeof(double));
+  }
+  double* ljx = (double*)calloc((size_t)N, sizeof(double));
+  double* ljy = (double*)calloc((size_t)N, sizeof(double));
+  double* lT = (double*)calloc((size_t)N, sizeof(double));
+  memset(lam_in, 0, sizeof(double) * 27 * (size_t)N);
+  for (long n = 0; n < N; ++n) {
+    if (w.solid[n]) continue;
+    const double r[2] = {w.rho1[n], w.rho2[n]};
+    const double rho = r[0] + r[1];
+    const double ux = w.jx[n] / rho, uy = w.jy[n] / rho;
+    const double Fx = w.Fx[0][n] + w.Fx[1][n], Fy = w.Fy[0][n] + w.Fy[1][n];
+    const double uHx = ux + Fx / (2.0 * rho), uHy = uy + Fy / (2.0 * rho);
+    double lux = 0.0, luy = 0.0;
+    for (int l = 0; l < 2; ++l) {
+      const double ulx = ux + tau * w.Fx[l][n] / r[l], uly = uy + tau * w.Fy[l][n] / r[l];
+      const double uu = ulx * ulx + uly * uly;
+      double lulx = 0.0, luly = 0.0;
+      for (int i = 0; i < 9; ++i) {
+        const double ls = lam_star[(long)(9 * l + i) * N + n];
+        lam_in[(long)(9 * l + i) * N + n] = (1.0 - om) * ls; /* f* = f + om (feq - f) */
+        const double lfeq = om * ls;
+        const double cu = CX[i] * ulx + CY[i] * uly;
+        /* feq = w rho_l (1 + 3 cu + 4.5 cu^2 - 1.5 u^2) */
+        lrho[l][n] += lfeq * weight_w(i) * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+        lulx += lfeq * weight_w(i) * r[l] * (3.0 * CX[i] + 9.0 * cu * CX[i] - 3.0 * ulx);
+        luly += lfeq * weight_w(i) * r[l] * (3.0 * CY[i] + 9.0 * cu * CY[i] - 3.0 * uly);
+      }
+      /* u_l = u + tau F_l / rho_l (Eq. shift) */
+      lux += lulx;
+      luy += luly;
+      lFx[l][n] += tau * lulx / r[l];
+      lFy[l][n] += tau * luly / r[l];
+      lrho[l][n] += -tau * (w.Fx[l][n] * lulx + w.Fy[l][n] * luly) / (r[l] * r[l]);
+    }
+    /* thermal collision, g^eq(T, u^(H)) (Eq. Teq) */
+    double luHx = 0.0, luHy = 0.0;
+    const double uuH = uHx * uHx + uHy * uHy;
+    for (int i = 0; i < 9; ++i) {
+      const double ls = lam_star[(long)(18 + i) * N + n];
+      lam_in[(long)(18 + i) * N + n] = (1.0 - omg) * ls;
+      const double lgeq = omg * ls;
+      const double cu = CX[i] * uHx + CY[i] * uHy;
+      lT[n] += lgeq * weight_w(i) * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uuH);
+      luHx += lgeq * weight_w(i) * w.T[n] * (3.0 * CX[i] + 9.0 * cu * CX[i] - 3.0 * uHx);
+      luHy += lgeq * weight_w(i) * w.T[n] * (3.0 * CY[i] + 9.0 * cu * CY[i] - 3.0 * uHy);
+    }
+    /* Nu seed: d/dS of cJ (<u^(H)_y T> - kappa <dT/dy>) / D; the dT/dy part is handled below */
+    if (cJ != 0.0 && nu_defined) {
+      luHy += cJ * w.T[n] / (nf * D);
+      lT[n] += cJ * uHy / (nf * D);
+    }
+    /* u^(H) = u + F / (2 rho) */
+    lux += luHx;
+    luy += luHy;
+    for (int l = 0; l < 2; ++l) {
+      lFx[l][n] += luHx / (2.0 * rho);
+      lFy[l][n] += luHy / (2.0 * rho);
+      lrho[l][n] += -(Fx * luHx + Fy * luHy) / (2.0 * rho * rho);
+    }
+    /* u = j / rho (Eq. velo) */
+    ljx[n] += lux / rho;
+    ljy[n] += luy / rho;
+    for (int l = 0; l < 2; ++l) lrho[l][n] += -(w.jx[n] * lux + w.jy[n] * luy) / (rho * rho);
+    /* external force rho_l (body_fx, alpha_g T) (Eq. alphaG) */
+    for (int l = 0; l < 2; ++l) {
+      lrho[l][n] += lFx[l][n] * prm->body_fx + lFy[l][n] * prm->alpha_g * w.T[n];
+      lT[n] += lFy[l][n] * prm->alpha_g * r[l];
+    }
+  }
+
+  /* Nu seed, the dT/dy term: d(sum_z dT/dy(z))/dT(x) with the mirror rule */
+  if (cJ != 0.0 && nu_defined) {
+    const double c = cJ * (-kappa) / (nf * D);
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const long n = (long)y * nx + x;
+        if (w.solid[n]) continue;
+        for (int s = 0; s < 2; ++s) {
+          const int sgn = s ? 1 : -1; /* neighbour above (+1) enters with +1/2, below with -1/2 */
+          int yy = y + sgn;
+          if (prm->periodic_y) yy = wrap(yy, ny);
+          const long nn = (long)yy * nx + x;
+          if (w.solid[nn])
+            lT[n] += c * 0.5 * sgn * (-1.0); /* mirror value 2 T_w - T(x) */
+          else
+            lT[nn] += c * 0.5 * sgn;
+        }
+      }
+    dTd += cJ * (-kappa * dB_dTdown_sum(prm, w.solid) / (nf * D));
+    /* Nu depends on T_down through D as well: dNu/dD = -Nu / D, dD/dT_down = kappa / H */
+    double obs[8];
+    orc_observables(prm, mask, S, obs);
+    dTd += cJ * (-obs[4] / dT);
+  }
+
+  /* 3. force adjoint: scatter dF_l(x)/dpsi(y) back to psi~ and psi at every fluid y */
+  double* lpt[2];
+  double* lpe[2];
+  for (int l = 0; l < 2; ++l) {
+    lpt[l] = (double*)calloc((size_t)N, sizeof(double));
+    lpe[l] = (double*)calloc((size_t)N, sizeof(double));
+  }
+  const double psit_w[2] = {prm->rho_wall[0] / rho0, prm->rho_wall[1] / rho0};
+  const double psie_w[2] = {psi_exp(prm->rho_wall[0], rho0), psi_exp(prm->rho_wall[1], rho0)};
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const long n = (long)y * nx + x;
+      if (w.solid[n]) continue;
+      for (int l = 0; l < 2; ++l) {
+        const int m = 1 - l;
+        const double ax = lFx[l][n], ay = lFy[l][n];
+        /* F^x_l = -G12 psi~_l(x) sum_NN w_i psi~_m(x + c_i) c_i */
+        double sx = 0.0, sy = 0.0;
+        for (int i = 0; i < 9; ++i) {
+          const double v = field_at(prm, w.solid, w.psit[m], psit_w[m], x + CX[i], y + CY[i]);
+          sx += weight_w(i) * v * CX[i];
+          sy += weight_w(i) * v * CY[i];
+          const long nb = fluid_at(prm, w.solid, x + CX[i], y + CY[i]);
+          if (nb >= 0) lpt[m][nb] += -prm->G12 * w.psit[l][n] * weight_w(i) * (CX[i] * ax + CY[i] * ay);
+        }
+        lpt[l][n] += -prm->G12 * (sx * ax + sy * ay);
+        /* F^a_l + F^r_l = -psi_l(x) sum_k (G^a w_k + G^r p_k) psi_l(x + c_k) c_k */
+        sx = sy = 0.0;
+        for (int k = 0; k < 25; ++k) {
+          const double a = prm->Ga[l] * (k < 9 ? weight_w(k) : 0.0) + prm->Gr[l] * weight_p(k);
+          const double v = field_at(prm, w.solid, w.psie[l], psie_w[l], x + CX[k], y + CY[k]);
+          sx += a * v * CX[k];
+          sy += a * v * CY[k];
+          const long nb = fluid_at(prm, w.solid, x + CX[k], y + CY[k]);
+          if (nb >= 0) lpe[l][nb] += -w.psie[l][n] * a * (CX[k] * ax + CY[k] * ay);
+        }
+        lpe[l][n] += -(sx * ax + sy * ay);
+      }
+    }
+
+  /* 4. pseudo-potentials to densities: psi~ = rho / rho0, psi = rho0 (1 - exp(-rho / rho0)) */
+  const double* rho[2] = {w.rho1, w.rho2};
+  for (long n = 0; n < N; ++n) {
+    if (w.solid[n]) continue;
+    for (int l = 0; l < 2; ++l) lrho[l][n] += lpt[l][n] / rho0 + lpe[l][n] * exp(-rho[l][n] / rho0);
+  }
+
+  /* 5. moments: rho_l = sum_i f_{l,i}, j = sum c_i f, T = sum_i g_i */
+  for (long n = 0; n < N; ++n) {
+    if (w.solid[n]) continue;
+    for (int i = 0; i < 9; ++i) {
+      for (int l = 0; l < 2; ++l) lam_in[(long)(9 * l + i) * N + n] += lrho[l][n] + CX[i] * ljx[n] + CY[i] * ljy[n];
+      lam_in[(long)(18 + i) * N + n] += lT[n];
+    }
+  }
+
+  if (dJ_dTdown) *dJ_dTdown += dTd;
+  for (int l = 0; l < 2; ++l) {
+    free(lFx[l]);
+    free(lFy[l]);
+    free(lrho[l]);
+    free(lpt[l]);
+    free(lpe[l]);
+  }
+  free(ljx);
+  free(ljy);
+  free(lT);
+  free(lam_star);
+  fwd_free(&w);
+  return 0;
+}
+
+int orc_adjoint_run(const orc_params* prm, const uint8_t* mask, const double* rho1, const double* rho2,
+                    const double* T0, long nsteps, double* J, double* dJ_dT0, double* dJ_dTdown) {
+  if (!valid(prm) || nsteps < 1) return -1;
+  const long N = (long)prm->nx * prm->ny;
+  const size_t SZ = 27 * (size_t)N;
+  double* states = (double*)malloc(sizeof(double) * SZ * (size_t)(nsteps + 1));
+  if (!states) return -2;
+  orc_init(prm, mask, rho1, rho2, T0, states);
+  double sumNu = 0.0, obs[8];
+  for (long t = 0; t < nsteps; ++t) {
+    orc_step(prm, mask, states + (size_t)t * SZ, states + (size_t)(t + 1) * SZ);
+    orc_observables(prm, mask, states + (size_t)(t + 1) * SZ, obs);
+    sumNu += obs[4];
+  }
+  *J = sumNu / (double)nsteps;
+  double* lam = (double*)calloc(SZ, sizeof(double));
+  double* lam2 = (double*)calloc(SZ, sizeof(double));
+  double dTd = 0.0;
+  /* lam_N = (1/N) dNu/dS_N; lam_t = Phi'(S_t)^T lam_{t+1} + (1/N) dNu/dS_t; lam_0 = Phi'(S_0)^T lam_1 */
+  orc_adjoint_step(prm, mask, states + (size_t)nsteps * SZ, NULL, 1.0 / (double)nsteps, lam, &dTd);
+  for (long t = nsteps - 1; t >= 0; --t) {
+    orc_adjoint_step(prm, mask, states + (size_t)t * SZ, lam, t >= 1 ? 1.0 / (double)nsteps : 0.0, lam2, &dTd);
+    double* tmp = lam;
+    lam = lam2;
+    lam2 = tmp;
+  }
+  /* S_0: g_i = w_i T0 at fluid nodes */
+  uint8_t* solid = (uint8_t*)malloc((size_t)N);
+  orc_solid_map(prm, mask, solid);
+  for (long n = 0; n < N; ++n) {
+    double s = 0.0;
+    if (!solid[n])
+      for (int i = 0; i < 9; ++i) s += weight_w(i) * lam[(long)(18 + i) * N + n];
+    dJ_dT0[n] = s;
+  }
+  *dJ_dTdown = dTd;
+  free(solid);
+  free(lam);
+  free(lam2);
+  free(states);
+  return 0;
+}

@@ -84,6 +84,18 @@ int orc_fields(const orc_params* prm, const uint8_t* mask, const double* state, 
  * nodes with a non-finite or non-positive density, out[7] number of fluid nodes. */
 int orc_observables(const orc_params* prm, const uint8_t* mask, const double* state, double* out);
 
+/* Discrete adjoint of one step (reverse mode): lam_in = (dS_{t+1}/dS_t)^T lam_out + cJ dNu(S_t)/dS_t,
+ * where S is the state S_t and lam_out (may be NULL = 0) the adjoint of S_{t+1}; all in the state
+ * layout.  *dJ_dTdown (may be NULL) is incremented by lam_out . dS_{t+1}/dT_down + cJ dNu(S_t)/dT_down. */
+int orc_adjoint_step(const orc_params* prm, const uint8_t* mask, const double* S, const double* lam_out, double cJ,
+                     double* lam_in, double* dJ_dTdown);
+
+/* J = (1/N) sum_{t=1..N} Nu(S_t) from the rest-equilibrium start of (rho1, rho2, T0), and its gradient
+ * with respect to the initial temperature field (dJ_dT0, nx*ny, 0 at solid nodes) and to T_down,
+ * by storing every state and running the reverse sweep. */
+int orc_adjoint_run(const orc_params* prm, const uint8_t* mask, const double* rho1, const double* rho2,
+                    const double* T0, long nsteps, double* J, double* dJ_dT0, double* dJ_dTdown);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,13 +74,17 @@ def posts_mask(nx, ny, height, width, period):
 
 
 def _disk_fields(nx, ny, centres, R):
-    """rho1, rho2 with sharp disks of component 1 (x periodic)."""
-    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    """rho1, rho2 with sharp disks of component 1 (x periodic); node (x, y) is inside a disk when
+    dx^2 + dy^2 <= R^2 with dx the periodic x distance."""
     inside = np.zeros((ny, nx), dtype=bool)
+    r = int(np.ceil(R)) + 1
     for cx, cy in centres:
-        dx = np.abs(x - cx)
+        ys = np.arange(max(0, int(np.floor(cy)) - r), min(ny, int(np.floor(cy)) + r + 2))
+        xs = np.arange(int(np.floor(cx)) - r, int(np.floor(cx)) + r + 2)
+        dx = np.abs(xs - cx)
         dx = np.minimum(dx, nx - dx)
-        inside |= dx * dx + (y - cy) ** 2 <= R * R
+        hit = dx[None, :] ** 2 + (ys[:, None] - cy) ** 2 <= R * R
+        inside[np.ix_(ys, xs % nx)] |= hit
     rho1 = np.where(inside, RHO_MAX, RHO_MIN)
     rho2 = np.where(inside, RHO_MIN, RHO_MAX)
     return rho1, rho2

@@ -21,7 +21,9 @@ _NAMES = {0: "LB_OK", -1: "LB_EINVAL", -2: "LB_ENOSPACE", -3: "LB_ECUDA", -4: "L
 # every symbol include/tlb.h declares
 EXPORTS = ("lb_workspace_size", "lb_init", "lb_step", "lb_observables", "lb_get_fields", "lb_get_state",
            "lb_set_state", "lb_sync", "lb_destroy", "lb_last_error", "lb_version", "lb_autotune", "lb_set_tile",
-           "lb_tile_info")
+           "lb_tile_info", "lb_batch_workspace_size", "lb_batch_init", "lb_batch_step", "lb_batch_configure",
+           "lb_batch_autotune", "lb_batch_info", "lb_batch_observables", "lb_batch_get_fields", "lb_batch_get_state",
+           "lb_batch_sync", "lb_batch_set_wait_budget", "lb_batch_destroy", "lb_batch_last_error")
 
 
 class LbError(RuntimeError):
@@ -75,6 +77,27 @@ def lib():
         L.lb_autotune.argtypes = [vp, i, ctypes.POINTER(i), dp, i]
         L.lb_set_tile.argtypes = [vp, i]
         L.lb_tile_info.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+        ip, ll = ctypes.POINTER(ctypes.c_int), ctypes.c_longlong
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        L.lb_batch_workspace_size.argtypes = [P, i, ip, ctypes.POINTER(sz)]
+        L.lb_batch_init.argtypes = [ctypes.POINTER(vp), P, i, pp, pp, pp, pp, vp, sz, vp]
+        L.lb_batch_step.argtypes = [vp, i]
+        L.lb_batch_configure.argtypes = [vp, i, i, i]
+        L.lb_batch_autotune.argtypes = [vp, i, ip, ip, ctypes.POINTER(ll), dp, i]
+        L.lb_batch_info.argtypes = [vp, ip, ip, ip, ip, ip]
+        L.lb_batch_observables.argtypes = [vp, i, ctypes.POINTER(LbObs)]
+        L.lb_batch_get_fields.argtypes = [vp, i, dp, dp, dp, dp, dp]
+        L.lb_batch_get_state.argtypes = [vp, i, dp, sz]
+        L.lb_batch_sync.argtypes = [vp]
+        L.lb_batch_set_wait_budget.argtypes = [vp, ll, i]
+        L.lb_batch_destroy.argtypes = [vp]
+        L.lb_batch_destroy.restype = None
+        L.lb_batch_last_error.argtypes = [vp]
+        L.lb_batch_last_error.restype = ctypes.c_char_p
+        for f in ("lb_batch_workspace_size", "lb_batch_init", "lb_batch_step", "lb_batch_configure",
+                  "lb_batch_autotune", "lb_batch_info", "lb_batch_observables", "lb_batch_get_fields",
+                  "lb_batch_get_state", "lb_batch_sync", "lb_batch_set_wait_budget"):
+            getattr(L, f).restype = ctypes.c_int
         L.lb_version.argtypes = []
         L.lb_version.restype = ctypes.c_char_p
         for f in ("lb_workspace_size", "lb_init", "lb_step", "lb_observables", "lb_get_fields", "lb_get_state",
@@ -197,6 +220,121 @@ class Lattice:
         if getattr(self, "_h", None) and self._h.value:
             lib().lb_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _bcheck(rc, b=None):
+    if rc != LB_OK:
+        raise LbError(rc, lib().lb_batch_last_error(b).decode())
+    return rc
+
+
+def batch_workspace_size(params_list, masks=None, precision=LB_FP32_SHIFTED):
+    n = len(params_list)
+    arr = (LbParams * n)(*[make_params(p, precision) for p in params_list])
+    hm = (ctypes.c_int * n)(*[int(masks is not None and masks[r] is not None) for r in range(n)])
+    out = ctypes.c_size_t()
+    _bcheck(lib().lb_batch_workspace_size(arr, n, hm, ctypes.byref(out)))
+    return out.value
+
+
+class Batch:
+    """An ensemble of independent lattices advanced together (lb_batch_* C ABI)."""
+
+    def __init__(self, params_list, rho1s, rho2s, T0s, masks=None, precision=LB_FP32_SHIFTED, device=None):
+        import torch
+
+        n = len(params_list)
+        self.n = n
+        self.params = [dict(p) for p in params_list]
+        self._cps = (LbParams * n)(*[make_params(p, precision) for p in params_list])
+        self.shapes = [(int(p["ny"]), int(p["nx"])) for p in params_list]
+        self._keep = []
+
+        def arr(a, shape):
+            x = np.ascontiguousarray(np.broadcast_to(a, shape), dtype=np.float64)
+            self._keep.append(x)
+            return x.ctypes.data_as(ctypes.c_void_p)
+
+        r1 = (ctypes.c_void_p * n)(*[arr(rho1s[r], self.shapes[r]) for r in range(n)])
+        r2 = (ctypes.c_void_p * n)(*[arr(rho2s[r], self.shapes[r]) for r in range(n)])
+        t0 = (ctypes.c_void_p * n)(*[arr(T0s[r], self.shapes[r]) for r in range(n)])
+        mk = (ctypes.c_void_p * n)()
+        for r in range(n):
+            if masks is not None and masks[r] is not None:
+                m = np.ascontiguousarray(masks[r], dtype=np.uint8)
+                self._keep.append(m)
+                mk[r] = m.ctypes.data_as(ctypes.c_void_p)
+        nbytes = batch_workspace_size(params_list, masks, precision)
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        with torch.cuda.device(dev):
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+            self.stream = torch.cuda.current_stream(dev)
+        self._b = ctypes.c_void_p()
+        _bcheck(lib().lb_batch_init(ctypes.byref(self._b), self._cps, n, mk, r1, r2, t0,
+                                    ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                    ctypes.c_void_p(self.stream.cuda_stream)))
+
+    def step(self, n=1):
+        _bcheck(lib().lb_batch_step(self._b, int(n)), self._b)
+        return self
+
+    def configure(self, schedule, tile=0, steps_per_launch=64):
+        _bcheck(lib().lb_batch_configure(self._b, int(schedule), int(tile), int(steps_per_launch)), self._b)
+
+    def info(self):
+        v = [ctypes.c_int() for _ in range(5)]
+        nc = lib().lb_batch_info(self._b, *(ctypes.byref(x) for x in v))
+        if nc < 0:
+            _bcheck(nc, self._b)
+        return {"items": v[0].value, "grid": v[1].value, "schedule": v[2].value, "tile": v[3].value,
+                "graphs": v[4].value, "tile_candidates": nc}
+
+    def autotune(self, trial_steps=16):
+        nc = self.info()["tile_candidates"]
+        ms = np.zeros(2 * nc)
+        sch, tile, taken = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        _bcheck(lib().lb_batch_autotune(self._b, int(trial_steps), ctypes.byref(sch), ctypes.byref(tile),
+                                        ctypes.byref(taken), _dp(ms), 2 * nc), self._b)
+        return {"schedule": sch.value, "tile": tile.value, "steps_taken": taken.value,
+                "ms_per_step": ms.reshape(2, nc).tolist()}
+
+    def observables(self, r, check=True):
+        o = LbObs()
+        rc = lib().lb_batch_observables(self._b, int(r), ctypes.byref(o))
+        if rc not in (LB_OK, LB_EUNSTABLE) or (check and rc != LB_OK):
+            _bcheck(rc, self._b)
+        return {"mass": np.array(o.mass[:]), "mom": np.array(o.mom[:]), "Nu": o.Nu, "E": o.E, "step": o.step,
+                "n_fluid": o.n_fluid, "n_bad": o.n_bad, "status": o.status}
+
+    def fields(self, r):
+        ny, nx = self.shapes[r]
+        out = {k: np.zeros((ny, nx)) for k in ("rho1", "rho2", "T", "ux", "uy")}
+        _bcheck(lib().lb_batch_get_fields(self._b, int(r), *(_dp(out[k]) for k in ("rho1", "rho2", "T", "ux", "uy"))),
+                self._b)
+        return out
+
+    def get_state(self, r):
+        ny, nx = self.shapes[r]
+        st = np.zeros((27, ny, nx))
+        _bcheck(lib().lb_batch_get_state(self._b, int(r), _dp(st), st.nbytes), self._b)
+        return st
+
+    def sync(self):
+        return lib().lb_batch_sync(self._b)
+
+    def set_wait_budget(self, cycles, withhold_item=-1):
+        _bcheck(lib().lb_batch_set_wait_budget(self._b, int(cycles), int(withhold_item)), self._b)
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            lib().lb_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
 
     def __del__(self):
         try:
