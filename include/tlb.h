@@ -162,6 +162,42 @@ int lb_tile_info(const lb_handle* h, int candidate, int* tx, int* ty, int* threa
 int lb_observables_static(const lb_params* p, const double* d_state, const uint8_t* d_mask, lb_obs* out,
                           void* stream);
 
+/* ---- Adjoint (not in the paper): reverse-mode gradient of the time-averaged Nusselt number
+ * J = (1/N) sum_{t=1..N} Nu(S_t) (Nu of Eq. NuTime) with respect to the initial temperature field T0
+ * and the bottom-wall temperature T_down, by the discrete adjoint of the fused step. */
+
+/* Storage layout of the handle's populations (also the layout of adjoint vectors): 27 planes of
+ * pitch * ny elements of elem_bytes (8: LB_FP64, 4: LB_FP32_SHIFTED), x fastest. */
+int lb_state_layout(const lb_handle* h, int* pitch, size_t* plane_elems, int* elem_bytes);
+
+/* Device workspace bytes lb_adjoint needs for n_steps steps with a checkpoint every ckpt_every steps
+ * (about (n_steps / ckpt_every + ckpt_every + 3) states; ckpt_every ~ sqrt(n_steps) minimises it).
+ * lb_adjoint_step needs lb_adjoint_workspace_size(h, 1, 1). */
+int lb_adjoint_workspace_size(const lb_handle* h, int n_steps, int ckpt_every, size_t* bytes);
+
+/* One reverse step at the handle's current state S_t:
+ *   d_lam = (dS_{t+1}/dS_t)^T d_lam_next + cJ dNu(S_t)/dS_t
+ * d_lam_next (NULL = 0) and d_lam: device vectors in the lb_state_layout layout and precision.
+ * *dJ_dTdown (host, may be NULL) receives d_lam_next . dS_{t+1}/dT_down + cJ dNu(S_t)/dT_down.
+ * Synchronous. */
+int lb_adjoint_step(lb_handle* h, const void* d_lam_next, void* d_lam, double cJ, void* d_adj_ws, size_t adj_bytes,
+                    double* dJ_dTdown);
+
+/* Treat the handle's current state as S_0 (the rest equilibrium of lb_init, g_i = w_i T0), run
+ * n_steps steps computing Nu after each, then the reverse sweep with sqrt-N checkpointing: every
+ * ckpt_every steps the state is stored; each segment is recomputed from its checkpoint and swept
+ * backwards.  J (host) receives the time-averaged Nu; dJ_dT0 (host nx*ny doubles, 0 at solid
+ * nodes) and dJ_dTdown (host) the gradient; with both NULL only J is computed.  The handle ends at
+ * S_{n_steps}.  d_adj_ws: caller-owned device memory of lb_adjoint_workspace_size bytes.
+ * Synchronous. */
+int lb_adjoint(lb_handle* h, int n_steps, int ckpt_every, void* d_adj_ws, size_t adj_bytes, double* J, double* dJ_dT0,
+               double* dJ_dTdown);
+
+/* Phase times of the last full lb_adjoint call of this thread (CUDA events on the handle's stream):
+ * out4[0] forward pass (steps + Nu) ms, out4[1] segment recomputation ms, out4[2] reverse sweep
+ * (adjoint steps) ms, out4[3] number of adjoint steps. */
+int lb_adjoint_timing(double* out4);
+
 /* ---- Batched ensembles (not in the paper): n independent lattices, each with its own lb_params
  * (size, couplings, Rayleigh number, precision equal for all), obstacle mask and state, advanced
  * together by one launch per step or by one persistent launch per K steps.  Every replica runs the

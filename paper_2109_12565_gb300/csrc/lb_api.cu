@@ -26,20 +26,6 @@ thread_local char g_err[512] = "no error";
 
 }  // namespace
 
-struct lb_handle {
-  lb_params p{};
-  Layout L{};
-  StepCfg cfg{};
-  cudaStream_t stream = nullptr;
-  cudaStream_t cap = nullptr;
-  unsigned char* ws = nullptr;
-  void* buf[2] = {nullptr, nullptr};
-  int cur = 0;
-  long long step = 0;
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  int tile = 0;  // step-kernel tile candidate (see lb_autotune)
-  char err[512] = "no error";
-};
 
 namespace {
 

@@ -148,3 +148,19 @@ inline const char* prepare_fields(lb_params& p, const uint8_t* mask, const doubl
 }
 
 }  // namespace tlb
+
+// Handle of one lattice (opaque to C callers; shared by the single-lattice and adjoint front ends).
+struct lb_handle {
+  lb_params p{};
+  tlb::Layout L{};
+  tlb::StepCfg cfg{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  unsigned char* ws = nullptr;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  long long step = 0;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int tile = 0;  // step-kernel tile candidate (see lb_autotune)
+  char err[512] = "no error";
+};

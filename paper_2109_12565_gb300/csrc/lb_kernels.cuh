@@ -205,10 +205,13 @@ __device__ __forceinline__ bool tile_phase_a(const S* __restrict__ fin, const KP
   return !any && no_wrap_x && no_wrap_y;
 }
 
-// Interaction + external forces at the node whose shared-memory centre is (cx, cy).
+// Interaction + external forces at the node whose shared-memory centre is (cx, cy), with the parts
+// the adjoint needs: the cross stencil sum cr = sum_NN w_i rho_m(x + c_i) c_i, the self stencil sum
+// s = sum_24 (G^a w_i + G^r p_i) psi_l(x + c_i) c_i and psi_l(x).
 template <class C, int TX, int TY, bool NEED_T>
-__device__ __forceinline__ void node_forces(const TileSmem<C, TX, TY, NEED_T>& sm, const KParams<C>& kp, int cx, int cy,
-                                            C r1, C r2, C T, C Fx[2], C Fy[2]) {
+__device__ __forceinline__ void node_force_parts(const TileSmem<C, TX, TY, NEED_T>& sm, const KParams<C>& kp, int cx,
+                                                 int cy, C r1, C r2, C T, C Fx[2], C Fy[2], C crx[2], C cry[2],
+                                                 C sx[2], C sy[2], C psl[2]) {
 #pragma unroll
   for (int l = 0; l < 2; ++l) {
     const int m = 1 - l;
@@ -218,8 +221,8 @@ __device__ __forceinline__ void node_forces(const TileSmem<C, TX, TY, NEED_T>& s
     const C e11 = sm.rho[m][cy + 1][cx + 1] - sm.rho[m][cy - 1][cx - 1];
     const C em1 = sm.rho[m][cy + 1][cx - 1] - sm.rho[m][cy - 1][cx + 1];
     const C w1 = C(1) / C(9), w2 = C(1) / C(36);
-    const C crx = w1 * e10 + w2 * (e11 - em1);
-    const C cry = w1 * e01 + w2 * (e11 + em1);
+    crx[l] = w1 * e10 + w2 * (e11 - em1);
+    cry[l] = w1 * e01 + w2 * (e11 + em1);
     const C rl = (l == 0) ? r1 : r2;
     // Eqs. FintAttrattive + FintRepulsive: -psi_l(x) sum_{24 links} (G^a w_i + G^r p_i) psi_l(x + c_i) c_i
     const C d10 = sm.psi[l][cy][cx + 1] - sm.psi[l][cy][cx - 1];
@@ -234,15 +237,22 @@ __device__ __forceinline__ void node_forces(const TileSmem<C, TX, TY, NEED_T>& s
     const C dm21 = sm.psi[l][cy + 1][cx - 2] - sm.psi[l][cy - 1][cx + 2];
     const C d22 = sm.psi[l][cy + 2][cx + 2] - sm.psi[l][cy - 2][cx - 2];
     const C dm22 = sm.psi[l][cy + 2][cx - 2] - sm.psi[l][cy - 2][cx + 2];
-    const C sx = kp.a1[l] * d10 + kp.a2[l] * (d11 - dm1) + kp.a4x2[l] * d20 +
-                 kp.a5[l] * (d12 - dm12 + C(2) * (d21 - dm21)) + kp.a8x2[l] * (d22 - dm22);
-    const C sy = kp.a1[l] * d01 + kp.a2[l] * (d11 + dm1) + kp.a4x2[l] * d02 +
-                 kp.a5[l] * (C(2) * (d12 + dm12) + d21 + dm21) + kp.a8x2[l] * (d22 + dm22);
-    const C psl = sm.psi[l][cy][cx];
+    sx[l] = kp.a1[l] * d10 + kp.a2[l] * (d11 - dm1) + kp.a4x2[l] * d20 +
+            kp.a5[l] * (d12 - dm12 + C(2) * (d21 - dm21)) + kp.a8x2[l] * (d22 - dm22);
+    sy[l] = kp.a1[l] * d01 + kp.a2[l] * (d11 + dm1) + kp.a4x2[l] * d02 +
+            kp.a5[l] * (C(2) * (d12 + dm12) + d21 + dm21) + kp.a8x2[l] * (d22 + dm22);
+    psl[l] = sm.psi[l][cy][cx];
     // Eq. alphaG (and the constant x acceleration)
-    Fx[l] = -kp.gx * rl * crx - psl * sx + rl * kp.body_fx;
-    Fy[l] = -kp.gx * rl * cry - psl * sy + rl * kp.alpha_g * T;
+    Fx[l] = -kp.gx * rl * crx[l] - psl[l] * sx[l] + rl * kp.body_fx;
+    Fy[l] = -kp.gx * rl * cry[l] - psl[l] * sy[l] + rl * kp.alpha_g * T;
   }
+}
+
+template <class C, int TX, int TY, bool NEED_T>
+__device__ __forceinline__ void node_forces(const TileSmem<C, TX, TY, NEED_T>& sm, const KParams<C>& kp, int cx, int cy,
+                                            C r1, C r2, C T, C Fx[2], C Fy[2]) {
+  C crx[2], cry[2], sx[2], sy[2], psl[2];
+  node_force_parts<C, TX, TY, NEED_T>(sm, kp, cx, cy, r1, r2, T, Fx, Fy, crx, cry, sx, sy, psl);
 }
 
 // Reciprocals of rho_1, rho_2 and rho_1 + rho_2 from one division.

@@ -23,7 +23,8 @@ EXPORTS = ("lb_workspace_size", "lb_init", "lb_step", "lb_observables", "lb_get_
            "lb_set_state", "lb_sync", "lb_destroy", "lb_last_error", "lb_version", "lb_autotune", "lb_set_tile",
            "lb_tile_info", "lb_batch_workspace_size", "lb_batch_init", "lb_batch_step", "lb_batch_configure",
            "lb_batch_autotune", "lb_batch_info", "lb_batch_observables", "lb_batch_get_fields", "lb_batch_get_state",
-           "lb_batch_sync", "lb_batch_set_wait_budget", "lb_batch_destroy", "lb_batch_last_error")
+           "lb_batch_sync", "lb_batch_set_wait_budget", "lb_batch_destroy", "lb_batch_last_error",
+           "lb_state_layout", "lb_adjoint_workspace_size", "lb_adjoint_step", "lb_adjoint", "lb_adjoint_timing")
 
 
 class LbError(RuntimeError):
@@ -97,6 +98,13 @@ def lib():
         for f in ("lb_batch_workspace_size", "lb_batch_init", "lb_batch_step", "lb_batch_configure",
                   "lb_batch_autotune", "lb_batch_info", "lb_batch_observables", "lb_batch_get_fields",
                   "lb_batch_get_state", "lb_batch_sync", "lb_batch_set_wait_budget"):
+            getattr(L, f).restype = ctypes.c_int
+        L.lb_state_layout.argtypes = [vp, ip, ctypes.POINTER(sz), ip]
+        L.lb_adjoint_workspace_size.argtypes = [vp, i, i, ctypes.POINTER(sz)]
+        L.lb_adjoint_step.argtypes = [vp, vp, vp, ctypes.c_double, vp, sz, dp]
+        L.lb_adjoint.argtypes = [vp, i, i, vp, sz, dp, dp, dp]
+        L.lb_adjoint_timing.argtypes = [dp]
+        for f in ("lb_state_layout", "lb_adjoint_workspace_size", "lb_adjoint_step", "lb_adjoint", "lb_adjoint_timing"):
             getattr(L, f).restype = ctypes.c_int
         L.lb_version.argtypes = []
         L.lb_version.restype = ctypes.c_char_p
@@ -215,6 +223,66 @@ class Lattice:
 
     def sync(self):
         _check(lib().lb_sync(self._h), self._h)
+
+    # -- adjoint
+    def state_layout(self):
+        pitch, plane, elem = ctypes.c_int(), ctypes.c_size_t(), ctypes.c_int()
+        _check(lib().lb_state_layout(self._h, ctypes.byref(pitch), ctypes.byref(plane), ctypes.byref(elem)), self._h)
+        return pitch.value, plane.value, elem.value
+
+    def to_device_vector(self, arr):
+        """[27, ny, nx] host array -> device tensor in the storage layout (for lb_adjoint_step)."""
+        import torch
+
+        pitch, _, elem = self.state_layout()
+        dt = torch.float64 if elem == 8 else torch.float32
+        t = torch.zeros((27, self.ny, pitch), dtype=dt, device=self.workspace.device)
+        t[:, :, :self.nx] = torch.from_numpy(np.ascontiguousarray(arr, dtype=np.float64)).to(dt)
+        return t
+
+    def from_device_vector(self, t):
+        return t[:, :, :self.nx].double().cpu().numpy()
+
+    def _adj_ws(self, n_steps, ckpt_every):
+        import torch
+
+        n = ctypes.c_size_t()
+        _check(lib().lb_adjoint_workspace_size(self._h, int(n_steps), int(ckpt_every), ctypes.byref(n)), self._h)
+        return torch.empty(n.value, dtype=torch.uint8, device=self.workspace.device), n.value
+
+    def adjoint_step(self, lam_next, cJ):
+        """lam_t (device tensor) and the dJ/dT_down increment of one reverse step at the current state;
+        lam_next: device tensor in the storage layout, or None."""
+        import torch
+
+        ws, nb = self._adj_ws(1, 1)
+        pitch, _, elem = self.state_layout()
+        dt = torch.float64 if elem == 8 else torch.float32
+        lam = torch.zeros((27, self.ny, pitch), dtype=dt, device=self.workspace.device)
+        d = ctypes.c_double()
+        nxt = None if lam_next is None else ctypes.c_void_p(lam_next.data_ptr())
+        _check(lib().lb_adjoint_step(self._h, nxt, ctypes.c_void_p(lam.data_ptr()), float(cJ),
+                                     ctypes.c_void_p(ws.data_ptr()), nb, ctypes.byref(d)), self._h)
+        return lam, d.value
+
+    def adjoint(self, n_steps, ckpt_every=None, gradient=True):
+        """(J, dJ/dT0 [ny, nx], dJ/dT_down) of J = time-averaged Nu over n_steps steps from the current
+        state, with sqrt-N checkpointing; with gradient=False only J (the other two are None)."""
+        ckpt = int(ckpt_every or max(1, round(n_steps ** 0.5)))
+        ws, nb = self._adj_ws(n_steps, ckpt)
+        J = ctypes.c_double()
+        g = np.zeros((self.ny, self.nx)) if gradient else None
+        d = ctypes.c_double()
+        _check(lib().lb_adjoint(self._h, int(n_steps), ckpt, ctypes.c_void_p(ws.data_ptr()), nb, ctypes.byref(J),
+                                _dp(g), ctypes.byref(d) if gradient else None), self._h)
+        return J.value, g, (d.value if gradient else None)
+
+    @staticmethod
+    def adjoint_timing():
+        """Phase times of the last adjoint(): forward ms, recompute ms, reverse ms, adjoint steps."""
+        out = np.zeros(4)
+        lib().lb_adjoint_timing(_dp(out))
+        return {"forward_ms": out[0], "recompute_ms": out[1], "reverse_ms": out[2], "adjoint_steps": int(out[3])}
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -341,3 +409,29 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def nusselt_mean(T0, T_down, params, rho1, rho2, n_steps, mask=None, precision=LB_FP64, ckpt_every=None):
+    """Differentiable J = time-averaged Nusselt number over n_steps steps started from the rest
+    equilibrium with temperature field T0 (torch tensor [ny, nx], float64) and bottom-wall
+    temperature T_down (0-d torch tensor); backward gives dJ/dT0 and dJ/dT_down from the library's
+    discrete adjoint (lb_adjoint)."""
+    import torch
+
+    class _NusseltMean(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, t0, td):
+            p = dict(params, T_down=float(td))
+            g = Lattice(p, rho1, rho2, t0.detach().cpu().double().numpy(), mask=mask, precision=precision)
+            J, dT0, dTd = g.adjoint(n_steps, ckpt_every)
+            g.close()
+            ctx.save_for_backward(torch.from_numpy(dT0).to(t0.dtype).to(t0.device),
+                                  torch.tensor(dTd, dtype=td.dtype, device=td.device))
+            return torch.tensor(J, dtype=t0.dtype, device=t0.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            dT0, dTd = ctx.saved_tensors
+            return grad_out * dT0, grad_out * dTd
+
+    return _NusseltMean.apply(T0, T_down)
