@@ -7,8 +7,14 @@ form; the FP64 form is measured on the same workload and reported beside it.
 
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
 on the launching stream; before every timed step a 512 MiB buffer is written
-(L2 flush), because the FP32 working set (113 MB) fits in the 135 MB L2.
+and another 512 MiB buffer is read (L2 flush: the FP32 working set, 113 MB,
+fits in the 135 MB L2; the read leaves L2 holding clean lines, so the timed
+step does not pay for writing back the flush's own data).
 MLUPS = nx * ny * K / sum(step times) / 1e6 (all lattice nodes).
+
+Other forms on the same line: the batched 64-replica ensemble (aggregate
+MLUPS), and the adjoint on the 512 x 256 emulsion (time of one reverse step
+and of the whole sqrt(N)-checkpointed gradient against forward steps).
 
 ``--impl reference`` times the FP64 CPU oracle (OpenMP build, all host
 cores) on the same workload and metric, each step a full lattice update.
@@ -133,6 +139,12 @@ class ClockSampler:
                 "max_util": max(util) if util else None}
 
 
+def flush_l2(flush):
+    """Write one buffer larger than L2, then read another (see the module docstring)."""
+    flush[0].fill_(1)
+    flush[1].max()  # a reduction that reads the whole buffer (no widened copy)
+
+
 def time_form(w, precision, steps, warmup, flush, tile=-1):
     """Per-step CUDA-event timing of the fused step on the Lattice's stream, L2 flushed before each step."""
     import torch
@@ -149,12 +161,12 @@ def time_form(w, precision, steps, warmup, flush, tile=-1):
     s = g.stream
     with torch.cuda.stream(s):
         for _ in range(warmup):
-            flush.fill_(1)
+            flush_l2(flush)
             g.step(1)
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for k in range(steps):
-            flush.fill_(k & 0xFF)
+            flush_l2(flush)
             ev[k][0].record(s)
             g.step(1)
             ev[k][1].record(s)
@@ -194,6 +206,40 @@ def time_batch(reps, steps, warmup, trial_steps=16):
     assert rc == 0
     return {"ms_total": ms, "ms_per_step": ms / steps, "nodes": nodes, "info": info, "tune": tune,
             "Nu_replica0": obs0["Nu"]}
+
+
+def time_adjoint(w, precision, n_steps, fwd_steps=200):
+    """Adjoint cost on workload w: mean forward step (CUDA events, K back-to-back single steps) against
+    the reverse-step time and the whole lb_adjoint (forward with Nu, recompute, reverse) per step."""
+    import torch
+
+    from paper_2109_12565_gb300 import lb
+
+    g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, mask=w.mask, precision=precision)
+    g.autotune(launches=5)
+    g.step(10)
+    s = g.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(fwd_steps):
+            g.step(1)
+        e1.record(s)
+        torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / fwd_steps
+    t0 = time.perf_counter()
+    J, gT0, gTd = g.adjoint(n_steps)
+    wall = time.perf_counter() - t0
+    tm = lb.Lattice.adjoint_timing()
+    g.close()
+    rev_ms = tm["reverse_ms"] / tm["adjoint_steps"]
+    total_ms = tm["forward_ms"] + tm["recompute_ms"] + tm["reverse_ms"]
+    return {"forward_step_ms": fwd_ms, "adjoint_step_ms": rev_ms, "adjoint_over_forward": rev_ms / fwd_ms,
+            "gradient_total_ms": total_ms, "gradient_wall_s": wall,
+            "amortised_over_forward": total_ms / (n_steps * fwd_ms), "n_steps": n_steps,
+            "checkpoints": max(1, round(n_steps ** 0.5)), "J": J, "dJ_dTdown": gTd,
+            "phases_ms": {k: tm[k] for k in ("forward_ms", "recompute_ms", "reverse_ms")}}
 
 
 def time_e2e(w, precision, steps, obs_every=500):
@@ -292,10 +338,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="fp32,fp64,batched", help="comma list of fp32, fp64, batched")
+    ap.add_argument("--forms", default="fp32,fp64,batched,adjoint",
+                    help="comma list of fp32, fp64, batched, adjoint")
     ap.add_argument("--fp64-steps", type=int, default=0, help="timed FP64 steps (default steps // 4)")
     ap.add_argument("--tile", type=int, default=-1, help="fixed tile candidate instead of autotuning")
     ap.add_argument("--batch-steps", type=int, default=200, help="timed steps of the 64-replica ensemble")
+    ap.add_argument("--adjoint-steps", type=int, default=2000, help="N of the adjoint gradient (512 x 256)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -320,7 +368,8 @@ def main():
     B.build()
     w = I.emulsion_1024x512()
     N = w.params["nx"] * w.params["ny"]
-    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = (torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda"),
+             torch.ones(FLUSH_BYTES, dtype=torch.uint8, device="cuda"))
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -334,6 +383,11 @@ def main():
         if "fp64" in forms_req:
             r64 = time_form(w, lb.LB_FP64, steps64, args.warmup, flush, args.tile)
         rb = time_batch(ens, args.batch_steps, args.warmup) if ens else None
+    radj = None
+    if "adjoint" in forms_req:
+        wa = I.emulsion_512x256()
+        radj = {"fp64": time_adjoint(wa, lb.LB_FP64, args.adjoint_steps),
+                "fp32_shifted": time_adjoint(wa, lb.LB_FP32_SHIFTED, args.adjoint_steps)}
     torch.cuda.synchronize()
     t32 = r32["ms_total"] if r32 else 0.0
     t64 = r64["ms_total"] if r64 else 0.0
@@ -377,6 +431,8 @@ def main():
             forms["fp64"]["alu_frac_of_nominal"] = forms["fp64"]["dp_tflops"] / FP64_NOMINAL_TFLOPS
     if r32 and r64:
         forms["fp32_over_fp64"] = mlups32 / mlups64
+    if radj:
+        forms["adjoint"] = dict(workload="emulsion_512x256", **{k: v for k, v in radj.items()})
     if rb:
         tb = rb["ms_total"]
         if dist:
@@ -391,7 +447,7 @@ def main():
                             "persistent_grid": rb["info"]["grid"], "graphs": rb["info"]["graphs"],
                             "autotune_ms_per_step": rb["tune"]["ms_per_step"], "steps": args.batch_steps,
                             "Nu_replica0": rb["Nu_replica0"]}
-    head = r32 or r64
+    head = r32 or r64 or {"ms_per_step": None}
     line = {
         "metric": METRIC, "value": mlups32 if r32 else mlups64, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps if r32 else steps64, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],

@@ -62,7 +62,19 @@ void drop_graphs(lb_handle* h) {
     }
 }
 
-void fill_cfg(lb_handle* h, const uint8_t* d_mask) { h->cfg = make_stepcfg(h->p, h->L.pitch, d_mask); }
+void fill_cfg(lb_handle* h, const uint8_t* d_mask) {
+  h->cfg = make_stepcfg(h->p, h->L.pitch, d_mask);
+  h->cfg.err = reinterpret_cast<int*>(h->ws + h->L.err_off);
+}
+
+// LB_ETIMEOUT when a kernel with bounded waits gave up (the state is then invalid).
+int check_err_word(lb_handle* h) {
+  int v = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(&v, h->cfg.err, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (v != 0) return fail(h, LB_ETIMEOUT, "a bounded device wait ran out; the state is invalid");
+  return LB_OK;
+}
 
 
 int build_graph(lb_handle* h, int parity) {
@@ -146,7 +158,7 @@ int lb_init(lb_handle** out, const lb_params* pin, const uint8_t* mask, const do
   };
   cudaError_t e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) return bail(fail(h, LB_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
-  e = cudaMemsetAsync(h->ws, 0, 2 * L.buf_bytes, h->stream);
+  e = cudaMemsetAsync(h->ws, 0, L.total, h->stream);  // buffers, partials and the error word start at zero
   if (e == cudaSuccess && mask) e = cudaMemcpyAsync(d_mask, mask, N, cudaMemcpyHostToDevice, h->stream);
   double* stage = static_cast<double*>(h->buf[1]);
   if (e == cudaSuccess) e = cudaMemcpyAsync(stage, rho1, N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
@@ -185,6 +197,7 @@ int lb_step(lb_handle* h, int n) {
 
 int lb_observables(lb_handle* h, lb_obs* out) {
   if (!h || !out) return fail(h, LB_EINVAL, "handle and out are required");
+  if (int rc = check_err_word(h)) return rc;
   double* part = reinterpret_cast<double*>(h->ws + h->L.part_off);
   double* dobs = reinterpret_cast<double*>(h->ws + h->L.obs_off);
   CUDA_TRY(h, launch(h, MODE_OBS, h->buf[h->cur], nullptr, part, h->stream));
@@ -317,7 +330,7 @@ int lb_sync(lb_handle* h) {
   if (!h) return fail(nullptr, LB_EINVAL, "handle is NULL");
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   CUDA_TRY(h, cudaGetLastError());
-  return LB_OK;
+  return check_err_word(h);
 }
 
 void lb_destroy(lb_handle* h) {

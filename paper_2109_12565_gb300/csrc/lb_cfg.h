@@ -33,6 +33,7 @@ struct StepCfg {
   double rho_bar[2], T_bar;   // storage shifts (0 in FP64)
   double kappa;               // (tau_g - 1/2) / 3, Eq. K
   double H;                   // wall-to-wall height ny - 2
+  int* err;                   // device error word for bounded waits (nullptr: kernels that wait are not used)
 };
 
 // Tile shapes (nodes per CTA in x and y; threads per CTA = TX * BY).
@@ -68,6 +69,13 @@ TileChoice tile_info_f64(int k);
 TileChoice tile_info_f32(int k);
 cudaError_t launch_step_tile_f64(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
 cudaError_t launch_step_tile_f32(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
+// Error codes a kernel writes to StepCfg::err (the host maps them to LB_ETIMEOUT).
+constexpr int kErrWaitTimeout = 1;
+// TMA-fed FP32 step (lb_tma.cu): candidates for the FP32 tile autotuner; they need StepCfg::err and
+// a lattice whose buffers are 16-byte aligned (always true for the workspace layout).
+int tma_count_f32();
+TileChoice tma_info_f32(int k);
+cudaError_t launch_step_tma_f32(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
 // Deterministic final reduction of n_blocks partials into kObsOut doubles.
 cudaError_t obs_finalize(const StepCfg& c, const double* partials, int n_blocks, double* out, cudaStream_t s);
 

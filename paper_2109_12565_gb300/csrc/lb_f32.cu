@@ -26,10 +26,17 @@ const Cand kCands[] = {
 };
 }  // namespace
 
-int tile_count_f32() { return (int)(sizeof kCands / sizeof kCands[0]); }
-TileChoice tile_info_f32(int k) { return kCands[k].t; }
+constexpr int kPlain = (int)(sizeof kCands / sizeof kCands[0]);
+
+// Candidates 0 .. kPlain-1: the plain tile kernel; kPlain .. : the TMA-fed pipelined kernel (lb_tma.cu),
+// which falls back to candidate 0 where it does not apply.
+int tile_count_f32() { return kPlain + tma_count_f32(); }
+TileChoice tile_info_f32(int k) { return k < kPlain ? kCands[k].t : tma_info_f32(k - kPlain); }
 cudaError_t launch_step_tile_f32(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s) {
-  return kCands[k].fn(c, fin, fout, s);
+  if (k < kPlain) return kCands[k].fn(c, fin, fout, s);
+  const cudaError_t e = launch_step_tma_f32(k - kPlain, c, fin, fout, s);
+  if (e == cudaErrorNotSupported) return kCands[0].fn(c, fin, fout, s);
+  return e;
 }
 
 cudaError_t init_f32(const StepCfg& c, const double* fields, void* buf, cudaStream_t s) {

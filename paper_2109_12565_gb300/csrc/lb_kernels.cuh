@@ -103,6 +103,15 @@ template <bool CG, class S> __device__ __forceinline__ S ld_pop(const S* p) {
   else return *p;
 }
 
+// Where phase B reads the populations of its own node: straight from the input buffer.
+template <class S, bool CG> struct GlobalPopSource {
+  const S* __restrict__ fin;
+  int plane;
+  __device__ __forceinline__ S operator()(int k, int idx, int /*tx*/, int /*ty*/) const {
+    return ld_pop<CG>(fin + idx + k * plane);
+  }
+};
+
 __device__ __forceinline__ int wrap_any(int a, int n) {
   int r = a % n;
   return r < 0 ? r + n : r;
@@ -320,10 +329,10 @@ __device__ __forceinline__ void node_collide(const KParams<C>& kp, const C f[9],
 
 // Phase B on one tile.  MODE_STEP: collide and push-store; MODE_OBS: accumulate the observables
 // of the node into acc[]; MODE_FIELDS: write rho1, rho2, T, u^(H) to aux planes.
-template <class S, class C, bool SHIFT, int MODE, bool FAST, int TX, int TY, int BY, bool CG>
-__device__ __forceinline__ void tile_phase_b(const S* __restrict__ fin, S* __restrict__ fout, const KParams<C>& kp,
-                                             int x0, int y0, const TileSmem<C, TX, TY, MODE != MODE_STEP>& sm,
-                                             double* __restrict__ aux, double acc[kObsSlots]) {
+template <class S, class C, bool SHIFT, int MODE, bool FAST, int TX, int TY, int BY, class Src>
+__device__ __forceinline__ void tile_phase_b(const Src& pop, S* __restrict__ fout, const KParams<C>& kp, int x0, int y0,
+                                             const TileSmem<C, TX, TY, MODE != MODE_STEP>& sm, double* __restrict__ aux,
+                                             double acc[kObsSlots]) {
   const int nx = kp.nx, ny = kp.ny, pitch = kp.pitch, plane = kp.plane;
   const C Tb = SHIFT ? kp.T_bar : C(0);
 #pragma unroll 1
@@ -344,18 +353,17 @@ __device__ __forceinline__ void tile_phase_b(const S* __restrict__ fin, S* __res
       continue;
     }
     const int idx = gy * pitch + gx;
-    const S* src = fin + idx;
     // moments (Sec. 2.1, 2.3): densities and momentum from phase A, T from the thermal populations;
     // in shifted storage the sums are deviations from the shift
     C f[9], h[9], g[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = C(ld_pop<CG>(src + (18 + i) * plane));
+    for (int i = 0; i < 9; ++i) g[i] = C(pop(18 + i, idx, tx, ty));
     const bool relax = !kp.tau_is_one;
     if (relax) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
-        f[i] = C(ld_pop<CG>(src + i * plane));
-        h[i] = C(ld_pop<CG>(src + (9 + i) * plane));
+        f[i] = C(pop(i, idx, tx, ty));
+        h[i] = C(pop(9 + i, idx, tx, ty));
       }
     }
     const C dr1 = sm.rho[0][cy][cx], dr2 = sm.rho[1][cy][cx];
@@ -442,10 +450,11 @@ __device__ __forceinline__ void tile_step(const S* __restrict__ fin, S* __restri
   constexpr int NT = TX * BY;
   const int tid = threadIdx.y * TX + threadIdx.x;
   const bool fast = tile_phase_a<S, C, SHIFT, MODE != MODE_STEP, TX, TY, NT, CG>(fin, kp, x0, y0, sm, tid);
+  const GlobalPopSource<S, CG> pop{fin, kp.plane};
   if (MODE == MODE_STEP && fast)
-    tile_phase_b<S, C, SHIFT, MODE, true, TX, TY, BY, CG>(fin, fout, kp, x0, y0, sm, aux, acc);
+    tile_phase_b<S, C, SHIFT, MODE, true, TX, TY, BY>(pop, fout, kp, x0, y0, sm, aux, acc);
   else
-    tile_phase_b<S, C, SHIFT, MODE, false, TX, TY, BY, CG>(fin, fout, kp, x0, y0, sm, aux, acc);
+    tile_phase_b<S, C, SHIFT, MODE, false, TX, TY, BY>(pop, fout, kp, x0, y0, sm, aux, acc);
 }
 
 // Block-wide deterministic sum of the observable accumulators into aux[slot * kObsSlots + v].

@@ -225,18 +225,22 @@ def test_init_errors():
 
 @pytest.mark.parametrize("precision", [lb.LB_FP64, lb.LB_FP32_SHIFTED])
 @pytest.mark.parametrize("periodic", [0, 1])
-def test_every_tile_candidate_gives_identical_results(precision, periodic):
-    """Tile shapes only change which CTA computes a node, never the arithmetic of a node: every
-    autotuner candidate must give bit-identical populations (fast interior path and general path)."""
-    nx, ny = 300, 130
+@pytest.mark.parametrize("nx,ny", [(300, 130), (277, 45)])
+def test_every_tile_candidate_gives_identical_results(precision, periodic, nx, ny):
+    """Tile shapes (and, in FP32, the TMA-fed pipelined kernels) only change which CTA computes a node
+    and how its populations reach shared memory, never the arithmetic of a node: every autotuner
+    candidate must give bit-identical populations (fast interior path, general path, ragged tiles,
+    periodic wrap)."""
     if periodic:
         y, x = np.mgrid[0:ny, 0:nx]
-        r1 = np.where(((x - 150) ** 2 + (y - 60) ** 2) < 30 ** 2, 1.4, 0.1)
-        params = dict(I.EMULSION_PARAMS, nx=nx, ny=ny, periodic_y=1, T_down=0.0, T_up=0.0, alpha_g=1e-4)
+        r1 = np.where(((x - nx // 2) ** 2 + (y - ny // 2) ** 2) < (ny // 3) ** 2, 1.4, 0.1)
+        # tau != 1 also runs the relaxation branch (populations read back in phase B)
+        params = dict(I.EMULSION_PARAMS, nx=nx, ny=ny, periodic_y=1, T_down=0.0, T_up=0.0, alpha_g=1e-4,
+                      tau=0.8, tau_g=0.9)
         T0 = 0.1 * np.sin(2 * np.pi * x / nx)
         mask = None
     else:
-        w = I.emulsion_hex(nx, ny, 6, 3, 0.7, 3e4, seed=9)
+        w = I.emulsion_hex(nx, ny, 6, 2, 0.6, 3e4, seed=9)
         params, r1, T0 = w.params, w.rho1, w.T0
         mask = I.posts_mask(nx, ny, 4, 5, 25)
     ref = None
@@ -270,3 +274,16 @@ def test_autotune_keeps_state_and_picks_a_candidate():
     h = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, precision=lb.LB_FP32_SHIFTED)
     h.step(8)
     np.testing.assert_array_equal(g.get_state(), h.get_state())
+
+
+def test_fresh_handle_reports_no_error_on_reused_memory():
+    """The workspace's error word starts at zero even when the caller's memory held other data."""
+    import torch
+
+    w = I.emulsion_small(nx=16, ny=16, n_drops=1, R=3.0)
+    junk = torch.full((lb.workspace_size(w.params) // 4 + 64,), -1, dtype=torch.int32, device="cuda")
+    del junk  # the caching allocator hands this memory to the next workspace
+    g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0)
+    g.step(2)
+    g.sync()
+    assert g.observables()["status"] == lb.LB_OK
