@@ -153,7 +153,8 @@ def time_form(w, precision, steps, warmup, flush, tile=-1):
 
     g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, mask=w.mask, precision=precision)
     if tile < 0:
-        tile, cand_ms = g.autotune(launches=10)
+        # the timed steps start with L2 flushed, so the candidates are timed the same way
+        tile, cand_ms = g.autotune(launches=10, scratch=flush[0])
     else:
         g.set_tile(tile)
         cand_ms = []

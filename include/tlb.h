@@ -56,11 +56,15 @@ extern "C" {
 #define LB_FP64 0           /* FP64 populations, FP64 arithmetic */
 #define LB_FP32_SHIFTED 1   /* FP32 deviations f - w_i rho_bar_l, g - w_i T_bar; FP32 arithmetic;
                                FP64 shift constants and FP64 reductions */
+#define LB_FP32_FP16T 2     /* as LB_FP32_SHIFTED, but the thermal deviations g - w_i T_bar are stored in
+                               FP16 (round to nearest on every store): 180 bytes of population traffic
+                               per lattice update instead of 216 (not in the paper).  Single lattices
+                               only: lb_batch_* and lb_adjoint* return LB_EINVAL for it. */
 
 typedef struct lb_params {
   int nx, ny;          /* lattice size including wall rows */
   int periodic_y;      /* 0: solid rows y = 0, ny-1; 1: periodic in y */
-  int precision;       /* LB_FP64 or LB_FP32_SHIFTED */
+  int precision;       /* LB_FP64, LB_FP32_SHIFTED or LB_FP32_FP16T */
   double tau;          /* fluid relaxation time (> 1/2), Eq. BGK */
   double tau_g;        /* thermal relaxation time (> 1/2), Eq. LBMg */
   double rho0;         /* reference density of psi~ and psi (> 0) */
@@ -71,8 +75,8 @@ typedef struct lb_params {
   double T_down, T_up; /* bottom / top wall temperature */
   double alpha_g;      /* buoyancy alpha * g, Eq. alphaG */
   double body_fx;      /* constant x acceleration on both components (0 in the paper's runs) */
-  double shift_rho[2]; /* LB_FP32_SHIFTED: rho_bar_l; NaN = mean initial density of the fluid nodes */
-  double shift_T;      /* LB_FP32_SHIFTED: T_bar; NaN = (T_down + T_up) / 2 */
+  double shift_rho[2]; /* FP32 forms: rho_bar_l; NaN = mean initial density of the fluid nodes */
+  double shift_T;      /* FP32 forms: T_bar; NaN = (T_down + T_up) / 2 */
 } lb_params;
 
 /* Observables of the current state S_t (pre-collision populations at step t). */
@@ -122,8 +126,9 @@ int lb_get_fields(lb_handle* h, double* rho1, double* rho2, double* T, double* u
 
 /* Copy the populations of S_t to / from host memory as 27 planes of nx*ny doubles (planes 0-8
  * f_{1,i}, 9-17 f_{2,i}, 18-26 g_i, D2Q9 order (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1)
- * (-1,-1) (1,-1)); solid nodes read as 0 and are ignored on write.  In LB_FP32_SHIFTED the
- * stored deviations are converted to full populations.  bytes must equal 27*nx*ny*8.
+ * (-1,-1) (1,-1)); solid nodes read as 0 and are ignored on write.  In the FP32 forms the
+ * stored deviations are converted to full populations (lb_set_state rounds them to the storage
+ * precision).  bytes must equal 27*nx*ny*8.
  * lb_set_state resets the step counter.  Synchronous. */
 int lb_get_state(lb_handle* h, double* host, size_t bytes);
 int lb_set_state(lb_handle* h, const double* host, size_t bytes);
@@ -135,6 +140,14 @@ int lb_set_state(lb_handle* h, const double* host, size_t bytes);
  * winning candidate; ms_per_candidate (may be NULL, n_slots entries) the mean milliseconds per
  * launch of each candidate.  Synchronous. */
 int lb_autotune(lb_handle* h, int launches, int* chosen, double* ms_per_candidate, int n_slots);
+
+/* The same autotuner for runs whose state does not stay in L2 between steps (not in the paper).
+ * Before each timed launch it writes scratch_bytes of the caller's device buffer d_scratch (give
+ * more than the L2 size; it is overwritten, not read), so every trial starts with the populations
+ * evicted from L2; only the launches are timed.  Returns LB_EINVAL without a scratch buffer.  The
+ * state and the step counter do not change.  Synchronous. */
+int lb_autotune_cold(lb_handle* h, int launches, void* d_scratch, size_t scratch_bytes, int* chosen,
+                     double* ms_per_candidate, int n_slots);
 
 /* Use tile candidate `candidate` for later lb_step calls (LB_EINVAL if out of range). */
 int lb_set_tile(lb_handle* h, int candidate);
@@ -167,7 +180,8 @@ int lb_observables_static(const lb_params* p, const double* d_state, const uint8
  * and the bottom-wall temperature T_down, by the discrete adjoint of the fused step. */
 
 /* Storage layout of the handle's populations (also the layout of adjoint vectors): 27 planes of
- * pitch * ny elements of elem_bytes (8: LB_FP64, 4: LB_FP32_SHIFTED), x fastest. */
+ * pitch * ny elements of elem_bytes (8: LB_FP64, 4: LB_FP32_SHIFTED), x fastest.  LB_EINVAL for
+ * LB_FP32_FP16T, whose planes do not share one element size. */
 int lb_state_layout(const lb_handle* h, int* pitch, size_t* plane_elems, int* elem_bytes);
 
 /* Device workspace bytes lb_adjoint needs for n_steps steps with a checkpoint every ckpt_every steps
@@ -265,6 +279,51 @@ const char* lb_last_error(const lb_handle* h);
 
 /* Library version string. */
 const char* lb_version(void);
+
+/* ---- Droplet topology (Sec. 2.4, "Delaunay triangulation"; run between steps, not part of the
+ * step).  Definitions:
+ *   D1  a droplet node is a fluid node with rho_1 > threshold (the paper's bubble threshold B_th);
+ *   D2  droplet nodes connect through the 4 nearest neighbours, x periodic, y periodic when
+ *       periodic_y;
+ *   D3  droplets are numbered 0, 1, ... in the order of their smallest node index y * nx + x;
+ *   D4  the centre of a droplet is the plain mean of its node coordinates, unwrapped relative to
+ *       its smallest node (offsets in (-nx/2, nx/2], likewise y when periodic), wrapped into the
+ *       lattice;
+ *   D5  the digital Voronoi colour of a fluid node is the id of the nearest centre (double
+ *       precision, minimum image, ties to the smaller id); solid nodes are -1;
+ *   D6  links: each 2 x 2 window of fluid nodes where three colours meet links the three pairs;
+ *       where four meet, the four pairs of neighbouring corners (the sides, not the diagonals).
+ * Results stay in a caller-owned device workspace; every result is independent of thread
+ * scheduling. */
+
+/* Device bytes of one droplet workspace for at most max_drops droplets (at most 16 * max_drops links,
+ * 32 per droplet). */
+int lb_droplets_workspace_size(const lb_handle* h, int max_drops, size_t* bytes);
+
+/* Analyse the current state into d_ws (256-byte aligned, ws_bytes from lb_droplets_workspace_size
+ * with the same max_drops): labels, centres, Voronoi colours, links.  *n_drops, *n_links (may be
+ * NULL) receive the counts.  LB_ENOSPACE when there are more droplets than max_drops or a droplet
+ * has more than 32 Voronoi neighbours.  Uses the handle's inactive buffer as staging; synchronous. */
+int lb_droplets(lb_handle* h, double threshold, int max_drops, void* d_ws, size_t ws_bytes, int* n_drops,
+                int* n_links);
+
+/* Copy results of lb_droplets to host arrays (any may be NULL): centres cx, cy and node counts
+ * size (n_drops each), links (2 * n_links ints: pairs a < b, ascending), label and color (nx * ny
+ * ints, x fastest: droplet id / -1, Voronoi colour / -1).  Synchronous. */
+int lb_droplets_get(lb_handle* h, const void* d_ws, size_t ws_bytes, double* cx, double* cy, long long* size,
+                    int* links, int* label, int* color);
+
+/* Plastic (T1) events between two analyses of this lattice (Sec. 2.4, diagonal flip of a
+ * quadrilateral): a droplet of the later analysis matches one of the earlier when each is the
+ * other's nearest centre within d_max.  Broken links: earlier links whose matched ends are no
+ * longer linked; arising links: later links (in earlier ids) that were not links; a T1 event is
+ * a broken link (a, b) with an arising link (c, d) such that c and d were linked to both a and b.
+ * counts4 = {matched, broken, arising, t1}; broken and arising receive up to cap pairs (earlier
+ * ids), t1 up to cap quadruples (a, b, c, d); all may be NULL.  d_scratch: device scratch; when
+ * too small, LB_ENOSPACE with counts4[0] = KiB needed.  Synchronous. */
+int lb_droplets_compare(lb_handle* h, const void* d_ws_prev, const void* d_ws_now, size_t ws_bytes, double d_max,
+                        void* d_scratch, size_t scratch_bytes, int* counts4, int* broken, int* arising, int* t1,
+                        int cap);
 
 #ifdef __cplusplus
 }

@@ -59,8 +59,14 @@ def lib(omp=False):
         L.orc_observables.argtypes = [P, u8, dp, dp]
         L.orc_adjoint_step.argtypes = [P, u8, dp, dp, ctypes.c_double, dp, dp]
         L.orc_adjoint_run.argtypes = [P, u8, dp, dp, dp, ctypes.c_long, dp, dp, dp]
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.orc_droplet_labels.argtypes = [P, u8, dp, ctypes.c_double, ip, ip]
+        L.orc_droplet_centres.argtypes = [P, ip, ctypes.c_int, dp, dp, ctypes.POINTER(ctypes.c_longlong)]
+        L.orc_digital_voronoi.argtypes = [P, u8, dp, dp, ctypes.c_int, ip]
+        L.orc_voronoi_links.argtypes = [P, ip, ip, ctypes.c_long, ctypes.POINTER(ctypes.c_long)]
         for f in ("orc_solid_map", "orc_init", "orc_forces", "orc_step", "orc_run", "orc_fields",
-                  "orc_observables", "orc_adjoint_step", "orc_adjoint_run"):
+                  "orc_observables", "orc_adjoint_step", "orc_adjoint_run", "orc_droplet_labels",
+                  "orc_droplet_centres", "orc_digital_voronoi", "orc_voronoi_links"):
             getattr(L, f).restype = ctypes.c_int
         _LIBS[key] = L
     return _LIBS[key]
@@ -212,3 +218,95 @@ def adjoint_run(params, rho1, rho2, T0, nsteps, mask=None):
     _check(lib().orc_adjoint_run(ctypes.byref(cp), mp, _dp(r1), _dp(r2), _dp(t0), int(nsteps), ctypes.byref(J),
                                  _dp(dT0), ctypes.byref(dTd)), "adjoint_run")
     return J.value, dT0, dTd.value
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def droplets(params, rho1, threshold, mask=None):
+    """Droplet topology of a density field (Sec. 2.4, definitions D1-D6 of tlb_droplets.c):
+    label [ny, nx] (droplet id or -1), centres cx, cy, sizes, Voronoi colours [ny, nx] and the
+    sorted link pairs [n_links, 2]."""
+    cp = make_params(params)
+    ny, nx = int(params["ny"]), int(params["nx"])
+    r1 = np.ascontiguousarray(rho1, dtype=np.float64)
+    m, mp = _mask(mask)
+    label = np.zeros((ny, nx), dtype=np.int32)
+    n = ctypes.c_int()
+    L = lib()
+    _check(L.orc_droplet_labels(ctypes.byref(cp), mp, _dp(r1), float(threshold), _ip(label), ctypes.byref(n)),
+           "droplet_labels")
+    M = n.value
+    cx, cy = np.zeros(max(M, 1)), np.zeros(max(M, 1))
+    size = np.zeros(max(M, 1), dtype=np.int64)
+    _check(L.orc_droplet_centres(ctypes.byref(cp), _ip(label), M, _dp(cx), _dp(cy),
+                                 size.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))), "droplet_centres")
+    color = np.zeros((ny, nx), dtype=np.int32)
+    _check(L.orc_digital_voronoi(ctypes.byref(cp), mp, _dp(cx), _dp(cy), M, _ip(color)), "digital_voronoi")
+    nl = ctypes.c_long()
+    _check(L.orc_voronoi_links(ctypes.byref(cp), _ip(color), None, 0, ctypes.byref(nl)), "voronoi_links")
+    links = np.zeros((max(nl.value, 1), 2), dtype=np.int32)
+    _check(L.orc_voronoi_links(ctypes.byref(cp), _ip(color), _ip(links), nl.value, ctypes.byref(nl)),
+           "voronoi_links")
+    return {"label": label, "n": M, "cx": cx[:M].copy(), "cy": cy[:M].copy(), "size": size[:M].copy(),
+            "color": color, "links": links[:nl.value].copy()}
+
+
+def _min_image(d, n):
+    if d > 0.5 * n:
+        d -= n
+    elif d < -0.5 * n:
+        d += n
+    return d
+
+
+def t1_compare(params, prev, now, d_max):
+    """Plastic (T1) events between two droplet analyses (Sec. 2.4, Fig. delaunayVoronoi b).
+
+    A droplet of ``now`` is matched to one of ``prev`` when each is the other's nearest centre
+    (minimum image, ties to the smaller id) and they lie within d_max.  Broken links: links of prev
+    whose two matched droplets are no longer linked; arising links: links of now (in prev ids)
+    absent from prev.  A T1 event is a broken link (a, b) and an arising link (c, d) with c and d
+    each linked to both a and b in prev: the diagonal of the quadrilateral a c b d flipped.
+    Returns sorted lists of pairs (prev ids) and of (a, b, c, d) quadruples."""
+    nx, ny, per_y = int(params["nx"]), int(params["ny"]), bool(params.get("periodic_y", 0))
+
+    def dist2(x0, y0, x1, y1):
+        dx = _min_image(x0 - x1, nx)
+        dy = _min_image(y0 - y1, ny) if per_y else y0 - y1
+        return dx * dx + dy * dy
+
+    def nearest(x, y, cx, cy):
+        best, bid = None, -1
+        for k in range(len(cx)):
+            d2 = dist2(x, y, cx[k], cy[k])
+            if bid < 0 or d2 < best:
+                best, bid = d2, k
+        return bid, best
+
+    n2p = {}
+    for j in range(now["n"]):
+        i, d2 = nearest(now["cx"][j], now["cy"][j], prev["cx"], prev["cy"])
+        if i < 0 or d2 > d_max * d_max:
+            continue
+        jj, _ = nearest(prev["cx"][i], prev["cy"][i], now["cx"], now["cy"])
+        if jj == j:
+            n2p[j] = i
+    p2n = {i: j for j, i in n2p.items()}
+    prev_links = {(int(a), int(b)) for a, b in prev["links"]}
+    now_links = {(int(a), int(b)) for a, b in now["links"]}
+    now_in_prev = set()
+    for c, d in now_links:
+        if c in n2p and d in n2p:
+            a, b = n2p[c], n2p[d]
+            now_in_prev.add((min(a, b), max(a, b)))
+    broken = sorted((a, b) for a, b in prev_links if a in p2n and b in p2n and (a, b) not in now_in_prev)
+    arising = sorted(e for e in now_in_prev if e not in prev_links)
+
+    def linked(a, b):
+        return (min(a, b), max(a, b)) in prev_links
+
+    t1 = sorted((a, b, c, d) for a, b in broken for c, d in arising
+                if linked(a, c) and linked(a, d) and linked(b, c) and linked(b, d))
+    return {"matched": len(n2p), "broken": broken, "arising": arising, "t1": t1}

@@ -10,7 +10,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "tlb_oracle.c")
+SRCS = [os.path.join(HERE, "tlb_oracle.c"), os.path.join(HERE, "tlb_droplets.c")]
 FLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC", "-shared", "-Wall"]
 
 
@@ -23,9 +23,9 @@ def build(force=False):
     for omp in (False, True):
         out = lib_path(omp)
         if force or not os.path.exists(out) or os.path.getmtime(out) < max(
-            os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "tlb_oracle.h"))
+            *(os.path.getmtime(s) for s in SRCS), os.path.getmtime(os.path.join(HERE, "tlb_oracle.h"))
         ):
-            cmd = ["gcc", *FLAGS, *(["-fopenmp"] if omp else []), SRC, "-o", out + ".tmp", "-lm"]
+            cmd = ["gcc", *FLAGS, *(["-fopenmp"] if omp else []), *SRCS, "-o", out + ".tmp", "-lm"]
             subprocess.check_call(cmd)
             os.replace(out + ".tmp", out)
         outs.append(out)

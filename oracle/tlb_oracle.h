@@ -96,6 +96,28 @@ int orc_adjoint_step(const orc_params* prm, const uint8_t* mask, const double* S
 int orc_adjoint_run(const orc_params* prm, const uint8_t* mask, const double* rho1, const double* rho2,
                     const double* T0, long nsteps, double* J, double* dJ_dT0, double* dJ_dTdown);
 
+/* ---- Droplet topology (Sec. 2.4; definitions D1-D6 in tlb_droplets.c). ---- */
+
+/* label[n]: droplet id of node n (ids in the order of each droplet's smallest node index) or -1
+ * (solid, or rho1 <= threshold); *n_drops: number of droplets. */
+int orc_droplet_labels(const orc_params* prm, const uint8_t* mask, const double* rho1, double threshold, int* label,
+                       int* n_drops);
+
+/* Centre of every droplet (plain mean of its node coordinates, periodic unwrapping relative to its
+ * smallest node) and its node count (size may be NULL). */
+int orc_droplet_centres(const orc_params* prm, const int* label, int n_drops, double* cx, double* cy,
+                        long long* size);
+
+/* Digital Voronoi tessellation: color[n] = id of the nearest centre (ties: smaller id), -1 at solid
+ * nodes. */
+int orc_digital_voronoi(const orc_params* prm, const uint8_t* mask, const double* cx, const double* cy, int n_drops,
+                        int* color);
+
+/* Delaunay links read off the 2 x 2 windows where three or four Voronoi colours meet: sorted unique
+ * pairs (a < b) into links[2 * max_links] (may be NULL to count only); returns -3 when more than
+ * max_links exist (*n_links is still the full count). */
+int orc_voronoi_links(const orc_params* prm, const int* color, int* links, long max_links, long* n_links);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,7 +79,7 @@ lb_adj1_kernel(const S* __restrict__ fin, const S* __restrict__ lam_out, S* __re
     const C r2 = sm.rho[1][cy][cx] + (SHIFT ? kp.rho_bar[1] : C(0));
     const C jx = sm.jx[ty][tx], jy = sm.jy[ty][tx];
     C Fx[2], Fy[2], crx[2], cry[2], sx[2], sy[2], psl[2];
-    node_force_parts<C, TX, TY, false>(sm, kp, cx, cy, r1, r2, T, Fx, Fy, crx, cry, sx, sy, psl);
+    node_force_parts<C>(sm, kp, cx, cy, r1, r2, T, Fx, Fy, crx, cry, sx, sy, psl);
     const C rho = r1 + r2;
     const C irho = C(1) / rho;
     const C ir[2] = {C(1) / r1, C(1) / r2};
@@ -484,7 +484,7 @@ int nu_coefs(lb_handle* h, const void* state, double* scratch16, double* nuc, do
 extern "C" {
 
 int lb_state_layout(const lb_handle* h, int* pitch, size_t* plane_elems, int* elem_bytes) {
-  if (!h) return LB_EINVAL;
+  if (!h || h->p.precision == LB_FP32_FP16T) return LB_EINVAL;
   if (pitch) *pitch = h->L.pitch;
   if (plane_elems) *plane_elems = (size_t)h->L.pitch * h->p.ny;
   if (elem_bytes) *elem_bytes = (int)h->L.elem;
@@ -492,7 +492,7 @@ int lb_state_layout(const lb_handle* h, int* pitch, size_t* plane_elems, int* el
 }
 
 int lb_adjoint_workspace_size(const lb_handle* h, int n_steps, int ckpt_every, size_t* bytes) {
-  if (!h || !bytes || n_steps < 1 || ckpt_every < 1) return LB_EINVAL;
+  if (!h || !bytes || n_steps < 1 || ckpt_every < 1 || h->p.precision == LB_FP32_FP16T) return LB_EINVAL;
   *bytes = adj_layout(h, n_steps, ckpt_every).total;
   return LB_OK;
 }
@@ -500,6 +500,7 @@ int lb_adjoint_workspace_size(const lb_handle* h, int n_steps, int ckpt_every, s
 int lb_adjoint_step(lb_handle* h, const void* d_lam_next, void* d_lam, double cJ, void* d_adj_ws, size_t adj_bytes,
                     double* dJ_dTdown) {
   if (!h || !d_lam || !d_adj_ws) return LB_EINVAL;
+  if (h->p.precision == LB_FP32_FP16T) return afail(h, LB_EINVAL, "the adjoint needs LB_FP64 or LB_FP32_SHIFTED");
   const AdjLayout A = adj_layout(h, 1, 1);
   if (adj_bytes < A.total || ((uintptr_t)d_adj_ws % kAlign) != 0) return afail(h, LB_ENOSPACE, "adjoint workspace too small");
   unsigned char* ws = static_cast<unsigned char*>(d_adj_ws);
@@ -530,6 +531,7 @@ int lb_adjoint_step(lb_handle* h, const void* d_lam_next, void* d_lam, double cJ
 int lb_adjoint(lb_handle* h, int n_steps, int ckpt_every, void* d_adj_ws, size_t adj_bytes, double* J, double* dJ_dT0,
                double* dJ_dTdown) {
   if (!h || n_steps < 1 || ckpt_every < 1 || !d_adj_ws || !J) return LB_EINVAL;
+  if (h->p.precision == LB_FP32_FP16T) return afail(h, LB_EINVAL, "the adjoint needs LB_FP64 or LB_FP32_SHIFTED");
   const AdjLayout A = adj_layout(h, n_steps, ckpt_every);
   if (adj_bytes < A.total || ((uintptr_t)d_adj_ws % kAlign) != 0) return afail(h, LB_ENOSPACE, "adjoint workspace too small");
   unsigned char* ws = static_cast<unsigned char*>(d_adj_ws);

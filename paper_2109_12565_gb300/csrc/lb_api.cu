@@ -45,14 +45,46 @@ int fail(lb_handle* h, int code, const char* fmt, ...) {
   } while (0)
 
 cudaError_t launch(const lb_handle* h, int mode, const void* fin, void* fout, double* aux, cudaStream_t s) {
+  const int pr = h->p.precision;
   if (mode == MODE_STEP)
-    return h->p.precision == LB_FP64 ? launch_step_tile_f64(h->tile, h->cfg, fin, fout, s)
-                                     : launch_step_tile_f32(h->tile, h->cfg, fin, fout, s);
-  return h->p.precision == LB_FP64 ? launch_f64(mode, h->cfg, fin, fout, aux, s)
-                                   : launch_f32(mode, h->cfg, fin, fout, aux, s);
+    return pr == LB_FP64 ? launch_step_tile_f64(h->tile, h->cfg, fin, fout, s)
+                         : (pr == LB_FP32_SHIFTED ? launch_step_tile_f32(h->tile, h->cfg, fin, fout, s)
+                                                  : launch_step_tile_f32h(h->tile, h->cfg, fin, fout, s));
+  return pr == LB_FP64 ? launch_f64(mode, h->cfg, fin, fout, aux, s)
+                       : (pr == LB_FP32_SHIFTED ? launch_f32(mode, h->cfg, fin, fout, aux, s)
+                                                : launch_f32h(mode, h->cfg, fin, fout, aux, s));
 }
 
-int tile_count(const lb_handle* h) { return h->p.precision == LB_FP64 ? tile_count_f64() : tile_count_f32(); }
+int tile_count(const lb_handle* h) {
+  const int pr = h->p.precision;
+  return pr == LB_FP64 ? tile_count_f64() : (pr == LB_FP32_SHIFTED ? tile_count_f32() : tile_count_f32h());
+}
+
+TileChoice tile_info(const lb_handle* h, int k) {
+  const int pr = h->p.precision;
+  return pr == LB_FP64 ? tile_info_f64(k) : (pr == LB_FP32_SHIFTED ? tile_info_f32(k) : tile_info_f32h(k));
+}
+
+cudaError_t init_buffer(const lb_handle* h, const double* fields, void* buf) {
+  const int pr = h->p.precision;
+  return pr == LB_FP64 ? init_f64(h->cfg, fields, buf, h->stream)
+                       : (pr == LB_FP32_SHIFTED ? init_f32(h->cfg, fields, buf, h->stream)
+                                                : init_f32h(h->cfg, fields, buf, h->stream));
+}
+
+cudaError_t plane_get(const lb_handle* h, int k, const void* buf, double* out) {
+  const int pr = h->p.precision;
+  return pr == LB_FP64 ? plane_get_f64(h->cfg, k, buf, out, h->stream)
+                       : (pr == LB_FP32_SHIFTED ? plane_get_f32(h->cfg, k, buf, out, h->stream)
+                                                : plane_get_f32h(h->cfg, k, buf, out, h->stream));
+}
+
+cudaError_t plane_put(const lb_handle* h, int k, const double* in, void* buf) {
+  const int pr = h->p.precision;
+  return pr == LB_FP64 ? plane_put_f64(h->cfg, k, in, buf, h->stream)
+                       : (pr == LB_FP32_SHIFTED ? plane_put_f32(h->cfg, k, in, buf, h->stream)
+                                                : plane_put_f32h(h->cfg, k, in, buf, h->stream));
+}
 
 void drop_graphs(lb_handle* h) {
   for (auto& g : h->gexec)
@@ -164,8 +196,7 @@ int lb_init(lb_handle** out, const lb_params* pin, const uint8_t* mask, const do
   if (e == cudaSuccess) e = cudaMemcpyAsync(stage, rho1, N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(stage + N, rho2, N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(stage + 2 * N, T0, N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = p.precision == LB_FP64 ? init_f64(h->cfg, stage, h->buf[0], h->stream)
-                                                   : init_f32(h->cfg, stage, h->buf[0], h->stream);
+  if (e == cudaSuccess) e = init_buffer(h, stage, h->buf[0]);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, L.buf_bytes, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return bail(fail(h, LB_ECUDA, "lb_init: %s", cudaGetErrorString(e)));
@@ -238,8 +269,7 @@ int lb_get_state(lb_handle* h, double* host, size_t bytes) {
   if (bytes != 27 * N * sizeof(double)) return fail(h, LB_EINVAL, "state needs %zu bytes", 27 * N * sizeof(double));
   double* stage = static_cast<double*>(h->buf[h->cur ^ 1]);
   for (int k = 0; k < 27; ++k) {
-    CUDA_TRY(h, h->p.precision == LB_FP64 ? plane_get_f64(h->cfg, k, h->buf[h->cur], stage, h->stream)
-                                          : plane_get_f32(h->cfg, k, h->buf[h->cur], stage, h->stream));
+    CUDA_TRY(h, plane_get(h, k, h->buf[h->cur], stage));
     CUDA_TRY(h, cudaMemcpyAsync(host + k * N, stage, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   }
@@ -253,15 +283,48 @@ int lb_set_state(lb_handle* h, const double* host, size_t bytes) {
   double* stage = static_cast<double*>(h->buf[h->cur ^ 1]);
   for (int k = 0; k < 27; ++k) {
     CUDA_TRY(h, cudaMemcpyAsync(stage, host + k * N, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(h, h->p.precision == LB_FP64 ? plane_put_f64(h->cfg, k, stage, h->buf[h->cur], h->stream)
-                                          : plane_put_f32(h->cfg, k, stage, h->buf[h->cur], h->stream));
+    CUDA_TRY(h, plane_put(h, k, stage, h->buf[h->cur]));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   }
   h->step = 0;
   return LB_OK;
 }
 
-int lb_autotune(lb_handle* h, int launches, int* chosen, double* ms_per_candidate, int n_slots) {
+namespace {
+
+// Times one trial of tile candidate h->tile: `launches` launches that read the current state and
+// write the inactive buffer.  Without scratch they run back to back (caches warm); with scratch
+// every launch is preceded by a write of scratch_bytes (caller memory larger than L2), which evicts
+// the state from L2, and only the launches themselves are timed.
+cudaError_t time_candidate(lb_handle* h, int launches, void* scratch, size_t scratch_bytes, cudaEvent_t e0,
+                           cudaEvent_t e1, float* ms_out) {
+  cudaError_t e = launch(h, MODE_STEP, h->buf[h->cur], h->buf[h->cur ^ 1], nullptr, h->stream);
+  float total = 0.0f;
+  if (!scratch) {
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int r = 0; r < launches && e == cudaSuccess; ++r)
+      e = launch(h, MODE_STEP, h->buf[h->cur], h->buf[h->cur ^ 1], nullptr, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&total, e0, e1);
+  } else {
+    for (int r = 0; r < launches && e == cudaSuccess; ++r) {
+      e = cudaMemsetAsync(scratch, r & 0xff, scratch_bytes, h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+      if (e == cudaSuccess) e = launch(h, MODE_STEP, h->buf[h->cur], h->buf[h->cur ^ 1], nullptr, h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      total += ms;
+    }
+  }
+  *ms_out = total / (float)launches;
+  return e;
+}
+
+int autotune_impl(lb_handle* h, int launches, void* scratch, size_t scratch_bytes, int* chosen,
+                  double* ms_per_candidate, int n_slots) {
   if (!h) return fail(nullptr, LB_EINVAL, "handle is NULL");
   if (launches < 1) return fail(h, LB_EINVAL, "launches must be >= 1");
   const int n = tile_count(h);
@@ -275,20 +338,12 @@ int lb_autotune(lb_handle* h, int launches, int* chosen, double* ms_per_candidat
   int rc = LB_OK;
   for (int k = 0; k < n && rc == LB_OK; ++k) {
     h->tile = k;
-    // every trial reads the current state and writes the inactive buffer: the state does not advance
-    cudaError_t e = launch(h, MODE_STEP, h->buf[h->cur], h->buf[h->cur ^ 1], nullptr, h->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-    for (int r = 0; r < launches && e == cudaSuccess; ++r)
-      e = launch(h, MODE_STEP, h->buf[h->cur], h->buf[h->cur ^ 1], nullptr, h->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.0f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    const cudaError_t e = time_candidate(h, launches, scratch, scratch_bytes, e0, e1, &ms);
     if (e != cudaSuccess) {
       rc = fail(h, LB_ECUDA, "autotune candidate %d: %s", k, cudaGetErrorString(e));
       break;
     }
-    ms /= (float)launches;
     if (ms_per_candidate) ms_per_candidate[k] = ms;
     if (k == 0 || ms < best_ms) {
       best_ms = ms;
@@ -307,6 +362,19 @@ int lb_autotune(lb_handle* h, int launches, int* chosen, double* ms_per_candidat
   return LB_OK;
 }
 
+}  // namespace
+
+int lb_autotune(lb_handle* h, int launches, int* chosen, double* ms_per_candidate, int n_slots) {
+  return autotune_impl(h, launches, nullptr, 0, chosen, ms_per_candidate, n_slots);
+}
+
+int lb_autotune_cold(lb_handle* h, int launches, void* d_scratch, size_t scratch_bytes, int* chosen,
+                     double* ms_per_candidate, int n_slots) {
+  if (!h) return fail(nullptr, LB_EINVAL, "handle is NULL");
+  if (!d_scratch || scratch_bytes == 0) return fail(h, LB_EINVAL, "cold autotuning needs a scratch buffer");
+  return autotune_impl(h, launches, d_scratch, scratch_bytes, chosen, ms_per_candidate, n_slots);
+}
+
 int lb_set_tile(lb_handle* h, int candidate) {
   if (!h) return fail(nullptr, LB_EINVAL, "handle is NULL");
   if (candidate < 0 || candidate >= tile_count(h)) return fail(h, LB_EINVAL, "tile candidate out of range");
@@ -319,7 +387,7 @@ int lb_tile_info(const lb_handle* h, int candidate, int* tx, int* ty, int* threa
   if (!h) return fail(nullptr, LB_EINVAL, "handle is NULL");
   if (candidate < 0) candidate = h->tile;
   if (candidate >= tile_count(h)) return LB_EINVAL;
-  const TileChoice t = h->p.precision == LB_FP64 ? tile_info_f64(candidate) : tile_info_f32(candidate);
+  const TileChoice t = tile_info(h, candidate);
   if (tx) *tx = t.tx;
   if (ty) *ty = t.ty;
   if (threads) *threads = t.tx * t.by;

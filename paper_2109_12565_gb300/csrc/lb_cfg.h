@@ -50,14 +50,18 @@ inline dim3 grid_for(int nx, int ny, int tx, int ty) {
 // MODE_FIELDS: aux = 5 planes of nx*ny doubles (rho1, rho2, T, ux, uy).
 cudaError_t launch_f64(int mode, const StepCfg& c, const void* fin, void* fout, double* aux, cudaStream_t s);
 cudaError_t launch_f32(int mode, const StepCfg& c, const void* fin, void* fout, double* aux, cudaStream_t s);
+cudaError_t launch_f32h(int mode, const StepCfg& c, const void* fin, void* fout, double* aux, cudaStream_t s);
 // Initial rest equilibria from 3 planes (rho1, rho2, T) of nx*ny doubles.
 cudaError_t init_f64(const StepCfg& c, const double* fields, void* buf, cudaStream_t s);
 cudaError_t init_f32(const StepCfg& c, const double* fields, void* buf, cudaStream_t s);
+cudaError_t init_f32h(const StepCfg& c, const double* fields, void* buf, cudaStream_t s);
 // One population plane k to / from nx*ny doubles (full populations; solid nodes 0 / ignored).
 cudaError_t plane_get_f64(const StepCfg& c, int k, const void* buf, double* out, cudaStream_t s);
 cudaError_t plane_get_f32(const StepCfg& c, int k, const void* buf, double* out, cudaStream_t s);
+cudaError_t plane_get_f32h(const StepCfg& c, int k, const void* buf, double* out, cudaStream_t s);
 cudaError_t plane_put_f64(const StepCfg& c, int k, const double* in, void* buf, cudaStream_t s);
 cudaError_t plane_put_f32(const StepCfg& c, int k, const double* in, void* buf, cudaStream_t s);
+cudaError_t plane_put_f32h(const StepCfg& c, int k, const double* in, void* buf, cudaStream_t s);
 // Step-kernel tile candidates for the autotuner: tile TX x TY nodes, TX * BY threads, at least MINB
 // resident CTAs per SM requested from the compiler.  Candidate 0 is the default.
 struct TileChoice {
@@ -65,10 +69,13 @@ struct TileChoice {
 };
 int tile_count_f64();
 int tile_count_f32();
+int tile_count_f32h();
 TileChoice tile_info_f64(int k);
 TileChoice tile_info_f32(int k);
+TileChoice tile_info_f32h(int k);
 cudaError_t launch_step_tile_f64(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
 cudaError_t launch_step_tile_f32(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
+cudaError_t launch_step_tile_f32h(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
 // Error codes a kernel writes to StepCfg::err (the host maps them to LB_ETIMEOUT).
 constexpr int kErrWaitTimeout = 1;
 // TMA-fed FP32 step (lb_tma.cu): candidates for the FP32 tile autotuner; they need StepCfg::err and
@@ -76,6 +83,11 @@ constexpr int kErrWaitTimeout = 1;
 int tma_count_f32();
 TileChoice tma_info_f32(int k);
 cudaError_t launch_step_tma_f32(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
+// Strip-marching TMA-fed FP32 step (lb_stream.cu): autotuner candidates after the TMA tile ones; they
+// need StepCfg::err, walls in y (periodic_y = 0) and nx >= 128, ny >= 8.
+int stream_count_f32();
+TileChoice stream_info_f32(int k);
+cudaError_t launch_step_stream_f32(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
 // Deterministic final reduction of n_blocks partials into kObsOut doubles.
 cudaError_t obs_finalize(const StepCfg& c, const double* partials, int n_blocks, double* out, cudaStream_t s);
 

@@ -1,0 +1,905 @@
+// Droplet topology of the current state on the GPU (TLBfind, arXiv 2109.12565, Sec. 2.4):
+// droplet regions (rho_1 above a threshold), their labels and centres of mass, the digital
+// Voronoi tessellation coloured by the nearest centre, the Delaunay links read off the points
+// where digital Voronoi cells meet, and the T1 (diagonal flip) events between two analyses.
+//
+// Definitions (the same as the oracle's):
+//   D1  droplet node: fluid node with rho_1 > B_th;
+//   D2  4-neighbour connectivity, x periodic, y periodic when periodic_y;
+//   D3  droplet ids 0, 1, ... in the order of each droplet's smallest node index y * nx + x;
+//   D4  centre = plain mean of the node coordinates, unwrapped relative to the smallest node;
+//   D5  Voronoi colour = id of the nearest centre (double, unfused dx*dx + dy*dy, minimum image,
+//       ties to the smaller id), -1 at solid nodes;
+//   D6  links: 2 x 2 windows with three colours give the three pairs, with four colours the four
+//       pairs of neighbouring corners.
+//
+// Pipeline (all on the caller's stream, no host round trip until the counts are read):
+//   fields (MODE_FIELDS of the step kernel) -> labels: union-find with atomicMin hooks, so every
+//   root ends as its component's smallest node -> ids: exclusive block scan of the root flags ->
+//   centres: 64-bit integer sums of the unwrapped offsets (exact, order independent) -> cell
+//   grid of the centres -> colours: nearest centre by rings of cells with an exact stopping
+//   distance -> links: a bounded adjacency set per droplet (atomicCAS), sorted per droplet,
+//   compacted by a scan.  Every result is independent of thread scheduling.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <vector>
+
+#include "lb_host.h"
+
+namespace tlb {
+namespace drops {
+
+constexpr int kMaxDeg = 32;     // links per droplet held in the adjacency set
+constexpr int kScanBlock = 1024;
+constexpr int kCell = 16;       // target edge of a centre-grid cell (nodes)
+constexpr int kErrDegree = 1;   // a droplet has more than kMaxDeg links
+constexpr int kErrDrops = 2;    // more droplets than max_drops
+constexpr int kErrUnion = 4;    // a union-find loop ran past its bound
+
+// Header at the start of the workspace (device-written counts, host-written sizes).
+struct Header {
+  int n_drops, n_links, err, max_drops;
+  int nx, ny, periodic_y, ncx, ncy;
+  int pad[7];
+};
+
+struct DLayout {
+  size_t hdr, lab, did, col, blk, cnt, sx, sy, root, cx, cy, adj, deg, lcount, loff, dblk, ccount, cstart, cfill,
+      citems, cblk, links, total;
+  long long N;
+  int nblk, max_drops, ncx, ncy, ncell, dnblk, cnblk;
+  long long max_links;
+};
+
+inline DLayout layout(int nx, int ny, int max_drops) {
+  DLayout L{};
+  L.N = (long long)nx * ny;
+  L.max_drops = max_drops;
+  L.nblk = (int)((L.N + kScanBlock - 1) / kScanBlock);
+  L.dnblk = (max_drops + kScanBlock - 1) / kScanBlock;
+  L.ncx = nx / kCell > 0 ? nx / kCell : 1;
+  L.ncy = ny / kCell > 0 ? ny / kCell : 1;
+  L.ncell = L.ncx * L.ncy;
+  L.cnblk = (L.ncell + kScanBlock - 1) / kScanBlock;
+  L.max_links = (long long)max_drops * kMaxDeg / 2;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += round_up(bytes, kAlign);
+    return o;
+  };
+  const size_t M = (size_t)max_drops;
+  L.hdr = take(sizeof(Header));
+  L.lab = take((size_t)L.N * 4);
+  L.did = take((size_t)L.N * 4);
+  L.col = take((size_t)L.N * 4);
+  L.blk = take((size_t)(L.nblk + 1) * 4);
+  L.cnt = take(M * 8);
+  L.sx = take(M * 8);
+  L.sy = take(M * 8);
+  L.root = take(M * 4);
+  L.cx = take(M * 8);
+  L.cy = take(M * 8);
+  L.adj = take(M * kMaxDeg * 4);
+  L.deg = take(M * 4);
+  L.lcount = take(M * 4);
+  L.loff = take(M * 4);
+  L.dblk = take((size_t)(L.dnblk + 1) * 4);
+  L.ccount = take((size_t)L.ncell * 4);
+  L.cstart = take((size_t)L.ncell * 4);
+  L.cfill = take((size_t)L.ncell * 4);
+  L.citems = take(M * 4);
+  L.cblk = take((size_t)(L.cnblk + 1) * 4);
+  L.links = take((size_t)L.max_links * 2 * 4);
+  L.total = off;
+  return L;
+}
+
+// Device view of one workspace.
+struct DView {
+  Header* hdr;
+  int *lab, *did, *col, *blk;
+  unsigned long long* cnt;
+  long long *sx, *sy;
+  int* root;
+  double *cx, *cy;
+  int *adj, *deg, *lcount, *loff, *dblk, *ccount, *cstart, *cfill, *citems, *cblk, *links;
+};
+
+inline DView view(void* ws, const DLayout& L) {
+  unsigned char* b = static_cast<unsigned char*>(ws);
+  DView v;
+  v.hdr = reinterpret_cast<Header*>(b + L.hdr);
+  v.lab = reinterpret_cast<int*>(b + L.lab);
+  v.did = reinterpret_cast<int*>(b + L.did);
+  v.col = reinterpret_cast<int*>(b + L.col);
+  v.blk = reinterpret_cast<int*>(b + L.blk);
+  v.cnt = reinterpret_cast<unsigned long long*>(b + L.cnt);
+  v.sx = reinterpret_cast<long long*>(b + L.sx);
+  v.sy = reinterpret_cast<long long*>(b + L.sy);
+  v.root = reinterpret_cast<int*>(b + L.root);
+  v.cx = reinterpret_cast<double*>(b + L.cx);
+  v.cy = reinterpret_cast<double*>(b + L.cy);
+  v.adj = reinterpret_cast<int*>(b + L.adj);
+  v.deg = reinterpret_cast<int*>(b + L.deg);
+  v.lcount = reinterpret_cast<int*>(b + L.lcount);
+  v.loff = reinterpret_cast<int*>(b + L.loff);
+  v.dblk = reinterpret_cast<int*>(b + L.dblk);
+  v.ccount = reinterpret_cast<int*>(b + L.ccount);
+  v.cstart = reinterpret_cast<int*>(b + L.cstart);
+  v.cfill = reinterpret_cast<int*>(b + L.cfill);
+  v.citems = reinterpret_cast<int*>(b + L.citems);
+  v.cblk = reinterpret_cast<int*>(b + L.cblk);
+  v.links = reinterpret_cast<int*>(b + L.links);
+  return v;
+}
+
+struct Geo {
+  int nx, ny, periodic_y;
+  const uint8_t* mask;
+};
+
+__device__ __forceinline__ bool is_solid(const Geo& g, int x, int y) {
+  if (!g.periodic_y && (y == 0 || y == g.ny - 1)) return true;
+  return g.mask != nullptr && g.mask[(long long)y * g.nx + x] != 0;
+}
+
+// ---------------------------------------------------------------- exclusive scan (3 kernels)
+
+// in[i] for i < n (0 beyond); bsum[b] = sum of block b.
+__global__ void scan_block_sums(const int* __restrict__ in, long long n, int* __restrict__ bsum) {
+  __shared__ int s_warp[kScanBlock / 32];
+  const long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
+  int v = i < n ? in[i] : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int w = s_warp[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = w;
+  }
+}
+
+// Block-wide inclusive scan of one value per thread (kScanBlock threads); *total (may be NULL)
+// receives the block total.
+__device__ __forceinline__ int block_inclusive_scan(int v, int* s_warp, int* total = nullptr) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) s_warp[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    int w = s_warp[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  const int add = warp > 0 ? s_warp[warp - 1] : 0;
+  if (total) *total = s_warp[kScanBlock / 32 - 1];
+  __syncthreads();
+  return v + add;
+}
+
+// One block: exclusive scan of bsum[0 .. nb) in place, bsum[nb] = total.
+__global__ void scan_block_offsets(int* __restrict__ bsum, int nb) {
+  __shared__ int s_warp[kScanBlock / 32];
+  int carry = 0;
+  for (int base = 0; base < nb; base += kScanBlock) {
+    const int i = base + threadIdx.x;
+    const int v = i < nb ? bsum[i] : 0;
+    int total = 0;
+    const int inc = block_inclusive_scan(v, s_warp, &total);
+    if (i < nb) bsum[i] = carry + inc - v;
+    carry += total;
+  }
+  if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+// out[i] = exclusive prefix of in[i] (out may alias in).
+__global__ void scan_apply(const int* in, long long n, const int* __restrict__ boff, int* out) {
+  __shared__ int s_warp[kScanBlock / 32];
+  const long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
+  const int v = i < n ? in[i] : 0;
+  const int inc = block_inclusive_scan(v, s_warp);
+  if (i < n) out[i] = boff[blockIdx.x] + inc - v;
+}
+
+cudaError_t exclusive_scan(const int* in, long long n, int* out, int* bsum, cudaStream_t s) {
+  const int nb = (int)((n + kScanBlock - 1) / kScanBlock);
+  if (nb == 0) return cudaMemsetAsync(bsum, 0, sizeof(int), s);
+  scan_block_sums<<<nb, kScanBlock, 0, s>>>(in, n, bsum);
+  scan_block_offsets<<<1, kScanBlock, 0, s>>>(bsum, nb);
+  scan_apply<<<nb, kScanBlock, 0, s>>>(in, n, bsum, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- labels (D1-D3)
+
+__global__ void label_init(const double* __restrict__ rho1, double threshold, Geo g, int* __restrict__ lab) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= (long long)g.nx * g.ny) return;
+  const int x = (int)(n % g.nx), y = (int)(n / g.nx);
+  lab[n] = (!is_solid(g, x, y) && rho1[n] > threshold) ? (int)n : -1;
+}
+
+__device__ __forceinline__ int find_root(const int* lab, int a) {
+  int r = a;
+  for (int k = 0; k < (1 << 26); ++k) {  // bounded: a parent chain is shorter than the lattice
+    const int p = lab[r];
+    if (p == r) return r;
+    r = p;
+  }
+  return -1;
+}
+
+// Hook the larger root under the smaller one until both nodes share a root.
+__device__ __forceinline__ void unite(int* lab, int a, int b, int* err) {
+  for (int k = 0; k < (1 << 20); ++k) {
+    a = find_root(lab, a);
+    b = find_root(lab, b);
+    if (a < 0 || b < 0) break;
+    if (a == b) return;
+    if (a < b) {
+      const int t = a;
+      a = b;
+      b = t;
+    }
+    const int old = atomicMin(&lab[a], b);
+    if (old == a) return;  // a was still a root: hooked
+    a = old;               // a was hooked meanwhile; continue from its new parent
+  }
+  atomicOr(err, kErrUnion);
+}
+
+__global__ void label_merge(Geo g, int* lab, int* err) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= (long long)g.nx * g.ny || lab[n] < 0) return;
+  const int x = (int)(n % g.nx), y = (int)(n / g.nx);
+  const int xr = x + 1 == g.nx ? 0 : x + 1;
+  const long long right = (long long)y * g.nx + xr;
+  if (right != n && lab[right] >= 0) unite(lab, (int)n, (int)right, err);
+  int yu = y + 1;
+  if (yu == g.ny) yu = g.periodic_y ? 0 : -1;
+  if (yu >= 0) {
+    const long long up = (long long)yu * g.nx + x;
+    if (up != n && lab[up] >= 0) unite(lab, (int)n, (int)up, err);
+  }
+}
+
+// Final labels (roots) and the root flags for the id scan (in did).
+__global__ void label_flatten(long long N, int* lab, int* __restrict__ flag) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int l = lab[n];
+  if (l < 0) {
+    flag[n] = 0;
+    return;
+  }
+  const int r = find_root(lab, (int)n);
+  lab[n] = r;  // every node of a chain resolves to the same root; concurrent writes store roots only
+  flag[n] = (r == (int)n) ? 1 : 0;
+}
+
+// did[n] = id of n's droplet (the scanned position of its root), -1 for background; root table.
+__global__ void label_ids(long long N, const int* __restrict__ lab, int* did, int* __restrict__ root, int max_drops,
+                          int* err) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int l = lab[n];
+  if (l < 0) return;
+  // did holds the exclusive scan of the root flags; a root keeps its own entry
+  if (l == (int)n) {
+    const int id = did[n];
+    if (id < max_drops) root[id] = (int)n;
+    else atomicOr(err, kErrDrops);
+  }
+}
+
+__global__ void label_ids_spread(long long N, const int* __restrict__ lab, int* did) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int l = lab[n];
+  // read the root's scanned position; a non-root's own slot is read by nobody, a root writes its
+  // own value back unchanged, so the in-place update is race free
+  did[n] = l < 0 ? -1 : did[l];
+}
+
+// ---------------------------------------------------------------- centres (D4)
+
+__device__ __forceinline__ long long min_image_i(long long d, int n) {
+  if (2 * d > n) d -= n;
+  if (2 * d <= -n) d += n;
+  return d;
+}
+
+__global__ void centre_sums(Geo g, const int* __restrict__ did, const int* __restrict__ root, int n_drops,
+                            unsigned long long* cnt, long long* sx, long long* sy) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= (long long)g.nx * g.ny) return;
+  const int d = did[n];
+  if (d < 0 || d >= n_drops) return;
+  const int r = root[d];
+  const long long x = n % g.nx, y = n / g.nx, rx = r % g.nx, ry = r / g.nx;
+  const long long dx = min_image_i(x - rx, g.nx);
+  const long long dy = g.periodic_y ? min_image_i(y - ry, g.ny) : (y - ry);
+  atomicAdd(cnt + d, 1ull);
+  atomicAdd(reinterpret_cast<unsigned long long*>(sx + d), (unsigned long long)dx);
+  atomicAdd(reinterpret_cast<unsigned long long*>(sy + d), (unsigned long long)dy);
+}
+
+__global__ void centre_final(Geo g, int n_drops, const int* __restrict__ root, const unsigned long long* __restrict__ cnt,
+                             const long long* __restrict__ sx, const long long* __restrict__ sy, double* cx, double* cy,
+                             int ncx, int ncy, int* __restrict__ ccount, int* __restrict__ dcell) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n_drops) return;
+  const int r = root[d];
+  const double rx = (double)(r % g.nx), ry = (double)(r / g.nx);
+  double x = __dadd_rn(rx, __ddiv_rn((double)sx[d], (double)cnt[d]));
+  double y = __dadd_rn(ry, __ddiv_rn((double)sy[d], (double)cnt[d]));
+  if (x < 0.0) x = __dadd_rn(x, (double)g.nx);
+  else if (x >= (double)g.nx) x = __dsub_rn(x, (double)g.nx);
+  if (g.periodic_y) {
+    if (y < 0.0) y = __dadd_rn(y, (double)g.ny);
+    else if (y >= (double)g.ny) y = __dsub_rn(y, (double)g.ny);
+  }
+  cx[d] = x;
+  cy[d] = y;
+  // cell of the centre: equal-width cells, nx / ncx by ny / ncy
+  int ix = (int)(x * ncx / g.nx), iy = (int)(y * ncy / g.ny);
+  ix = ix < 0 ? 0 : (ix >= ncx ? ncx - 1 : ix);
+  iy = iy < 0 ? 0 : (iy >= ncy ? ncy - 1 : iy);
+  const int c = iy * ncx + ix;
+  dcell[d] = c;
+  atomicAdd(ccount + c, 1);
+}
+
+__global__ void cell_fill(int n_drops, const int* __restrict__ dcell, const int* __restrict__ cstart, int* cfill,
+                          int* __restrict__ citems) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n_drops) return;
+  const int c = dcell[d];
+  citems[cstart[c] + atomicAdd(cfill + c, 1)] = d;
+}
+
+// ---------------------------------------------------------------- nearest centre (D5)
+
+struct Grid {
+  const double *cx, *cy;
+  const int *cstart, *ccount, *citems;
+  int ncx, ncy;
+  double cw_min;  // smaller cell edge
+};
+
+// Nearest centre to (x, y): rings of cells around the point's cell until no unvisited cell can hold a
+// closer centre.  A cell at ring distance >= r + 1 lies >= r cell edges away in x or y, so after ring
+// r every centre not yet seen is farther than (r - 1) * cw_min (one ring of margin for the rounding
+// of the cell index).  Ties keep the smaller id.
+__device__ int nearest_centre(const Geo& g, const Grid& G, double x, double y, double* best_out) {
+  const double hx = 0.5 * g.nx, hy = 0.5 * g.ny;
+  int ix = (int)(x * G.ncx / g.nx), iy = (int)(y * G.ncy / g.ny);
+  ix = ix < 0 ? 0 : (ix >= G.ncx ? G.ncx - 1 : ix);
+  iy = iy < 0 ? 0 : (iy >= G.ncy ? G.ncy - 1 : iy);
+  double best = 0.0;
+  int best_id = -1;
+  const int rmax = (G.ncx > G.ncy ? G.ncx : G.ncy) + 1;
+  for (int r = 0; r <= rmax; ++r) {
+    for (int jy = iy - r; jy <= iy + r; ++jy) {
+      int cyi = jy;
+      if (g.periodic_y) cyi = ((jy % G.ncy) + G.ncy) % G.ncy;
+      else if (jy < 0 || jy >= G.ncy) continue;
+      const bool edge_row = (jy == iy - r) || (jy == iy + r);
+      for (int jx = ix - r; jx <= ix + r; jx += (edge_row || r == 0) ? 1 : 2 * r) {
+        const int cxi = ((jx % G.ncx) + G.ncx) % G.ncx;
+        const int c = cyi * G.ncx + cxi;
+        const int s = G.cstart[c], e = s + G.ccount[c];
+        for (int k = s; k < e; ++k) {
+          const int d = G.citems[k];
+          double dx = __dsub_rn(x, G.cx[d]);
+          if (dx > hx) dx = __dsub_rn(dx, (double)g.nx);
+          else if (dx < -hx) dx = __dadd_rn(dx, (double)g.nx);
+          double dy = __dsub_rn(y, G.cy[d]);
+          if (g.periodic_y) {
+            if (dy > hy) dy = __dsub_rn(dy, (double)g.ny);
+            else if (dy < -hy) dy = __dadd_rn(dy, (double)g.ny);
+          }
+          const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+          if (best_id < 0 || d2 < best || (d2 == best && d < best_id)) {
+            best = d2;
+            best_id = d;
+          }
+        }
+      }
+    }
+    if (best_id >= 0 && r >= 1) {
+      const double bound = (double)(r - 1) * G.cw_min;
+      if (best < bound * bound) break;
+    }
+  }
+  if (best_out) *best_out = best;
+  return best_id;
+}
+
+__global__ void voronoi_colour(Geo g, Grid G, int n_drops, int* __restrict__ col) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= (long long)g.nx * g.ny) return;
+  const int x = (int)(n % g.nx), y = (int)(n / g.nx);
+  if (is_solid(g, x, y) || n_drops == 0) {
+    col[n] = -1;
+    return;
+  }
+  col[n] = nearest_centre(g, G, (double)x, (double)y, nullptr);
+}
+
+// ---------------------------------------------------------------- links (D6)
+
+__device__ __forceinline__ void adj_insert(int* adj, int* deg, int a, int b, int* err) {
+  int* slots = adj + (long long)a * kMaxDeg;
+  for (int k = 0; k < kMaxDeg; ++k) {
+    const int v = atomicCAS(slots + k, -1, b);
+    if (v == -1) {
+      atomicAdd(deg + a, 1);
+      return;
+    }
+    if (v == b) return;
+  }
+  atomicOr(err, kErrDegree);
+}
+
+__global__ void voronoi_links(Geo g, const int* __restrict__ col, int* adj, int* deg, int* err) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= (long long)g.nx * g.ny) return;
+  const int x = (int)(n % g.nx), y = (int)(n / g.nx);
+  if (!g.periodic_y && y == g.ny - 1) return;
+  const int x1 = x + 1 == g.nx ? 0 : x + 1, y1 = y + 1 == g.ny ? 0 : y + 1;
+  // corners in cyclic order: 00, 10, 11, 01
+  const int c[4] = {col[(long long)y * g.nx + x], col[(long long)y * g.nx + x1], col[(long long)y1 * g.nx + x1],
+                    col[(long long)y1 * g.nx + x]};
+  if (c[0] < 0 || c[1] < 0 || c[2] < 0 || c[3] < 0) return;
+  int dist[4], k = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    bool seen = false;
+    for (int j = 0; j < k; ++j) seen |= dist[j] == c[i];
+    if (!seen) dist[k++] = c[i];
+  }
+  if (k == 3) {
+    const int p[3][2] = {{dist[0], dist[1]}, {dist[1], dist[2]}, {dist[0], dist[2]}};
+    for (int i = 0; i < 3; ++i) {
+      adj_insert(adj, deg, p[i][0], p[i][1], err);
+      adj_insert(adj, deg, p[i][1], p[i][0], err);
+    }
+  } else if (k == 4) {
+    for (int i = 0; i < 4; ++i) {
+      const int a = c[i], b = c[(i + 1) & 3];
+      adj_insert(adj, deg, a, b, err);
+      adj_insert(adj, deg, b, a, err);
+    }
+  }
+}
+
+// Sort each adjacency set (ascending; empty slots last) and count its links to larger ids.
+__global__ void adj_sort(int n_drops, int* adj, const int* __restrict__ deg, int* __restrict__ lcount) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n_drops) return;
+  int* a = adj + (long long)d * kMaxDeg;
+  const int m = deg[d] < kMaxDeg ? deg[d] : kMaxDeg;
+  for (int i = 1; i < m; ++i) {
+    const int v = a[i];
+    int j = i - 1;
+    while (j >= 0 && a[j] > v) {
+      a[j + 1] = a[j];
+      --j;
+    }
+    a[j + 1] = v;
+  }
+  int c = 0;
+  for (int i = 0; i < m; ++i) c += a[i] > d ? 1 : 0;
+  lcount[d] = c;
+}
+
+__global__ void links_write(int n_drops, const int* __restrict__ adj, const int* __restrict__ deg,
+                            const int* __restrict__ loff, int* __restrict__ links) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n_drops) return;
+  const int* a = adj + (long long)d * kMaxDeg;
+  const int m = deg[d] < kMaxDeg ? deg[d] : kMaxDeg;
+  int o = loff[d];
+  for (int i = 0; i < m; ++i)
+    if (a[i] > d) {
+      links[2 * o] = d;
+      links[2 * o + 1] = a[i];
+      ++o;
+    }
+}
+
+__global__ void write_header(Header* h, const int* __restrict__ dscan_total, const int* __restrict__ lscan_total,
+                             int max_drops, int stage) {
+  if (stage == 0) {
+    const int m = *dscan_total;
+    h->n_drops = m < max_drops ? m : max_drops;
+    if (m > max_drops) h->err |= kErrDrops;
+  } else {
+    h->n_links = *lscan_total;
+  }
+}
+
+// ---------------------------------------------------------------- T1 comparison
+
+__device__ __forceinline__ bool has_link(const int* adj, const int* deg, int a, int b) {
+  const int* s = adj + (long long)a * kMaxDeg;
+  const int m = deg[a] < kMaxDeg ? deg[a] : kMaxDeg;
+  for (int i = 0; i < m; ++i)
+    if (s[i] == b) return true;
+  return false;
+}
+
+// match[j] = i when droplet j of `from` and droplet i of `to` are each other's nearest centre
+// within d_max; one pass per direction (near[] holds the one-directional nearest).
+__global__ void nearest_other(Geo g, Grid to, int n_from, const double* __restrict__ fx, const double* __restrict__ fy,
+                              double d2max, int* __restrict__ near) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_from) return;
+  double best = 0.0;
+  const int i = nearest_centre(g, to, fx[j], fy[j], &best);
+  near[j] = (i >= 0 && best <= d2max) ? i : -1;
+}
+
+__global__ void mutual(int n_now, const int* __restrict__ near_np, const int* __restrict__ near_pn,
+                       int* __restrict__ n2p) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_now) return;
+  const int i = near_np[j];
+  n2p[j] = (i >= 0 && near_pn[i] == j) ? i : -1;
+}
+
+__global__ void invert(int n_now, const int* __restrict__ n2p, int* __restrict__ p2n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_now) return;
+  if (n2p[j] >= 0) p2n[n2p[j]] = j;
+}
+
+// mode 0: broken links of prev (per prev droplet a, links a < b); mode 1: arising links (per now
+// droplet c, links c < d, written in prev ids).  count pass (out == nullptr) and write pass.
+__global__ void link_changes(int mode, int n, const int* __restrict__ adj_self, const int* __restrict__ deg_self,
+                             const int* __restrict__ adj_other, const int* __restrict__ deg_other,
+                             const int* __restrict__ map, const int* __restrict__ cnt_off, int* __restrict__ counts,
+                             int* __restrict__ out) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  const int* s = adj_self + (long long)a * kMaxDeg;
+  const int m = deg_self[a] < kMaxDeg ? deg_self[a] : kMaxDeg;
+  int c = 0, o = out ? cnt_off[a] : 0;
+  for (int i = 0; i < m; ++i) {
+    const int b = s[i];
+    if (b <= a) continue;
+    const int ma = map[a], mb = map[b];
+    if (ma < 0 || mb < 0) continue;
+    if (has_link(adj_other, deg_other, ma, mb)) continue;
+    if (out) {
+      const int lo = mode == 0 ? a : (ma < mb ? ma : mb), hi = mode == 0 ? b : (ma < mb ? mb : ma);
+      out[2 * (o + c)] = lo;
+      out[2 * (o + c) + 1] = hi;
+    }
+    ++c;
+  }
+  if (!out) counts[a] = c;
+}
+
+// T1 events: per broken link (a, b), the pairs (c, d) of common prev neighbours of a and b that are
+// not linked in prev but are linked now (both matched).
+__global__ void t1_events(int n_broken, const int* __restrict__ broken, const int* __restrict__ adj_p,
+                          const int* __restrict__ deg_p, const int* __restrict__ adj_n, const int* __restrict__ deg_n,
+                          const int* __restrict__ p2n, const int* __restrict__ cnt_off, int* __restrict__ counts,
+                          int* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_broken) return;
+  const int a = broken[2 * k], b = broken[2 * k + 1];
+  const int* sa = adj_p + (long long)a * kMaxDeg;
+  const int ma = deg_p[a] < kMaxDeg ? deg_p[a] : kMaxDeg;
+  int cnt = 0, o = out ? cnt_off[k] : 0;
+  for (int i = 0; i < ma; ++i) {
+    const int c = sa[i];
+    if (!has_link(adj_p, deg_p, b, c)) continue;
+    for (int j = i + 1; j < ma; ++j) {
+      const int d = sa[j];
+      if (!has_link(adj_p, deg_p, b, d) || has_link(adj_p, deg_p, c, d)) continue;
+      const int nc = p2n[c], nd = p2n[d];
+      if (nc < 0 || nd < 0 || !has_link(adj_n, deg_n, nc, nd)) continue;
+      if (out) {
+        out[4 * (o + cnt)] = a;
+        out[4 * (o + cnt) + 1] = b;
+        out[4 * (o + cnt) + 2] = c < d ? c : d;
+        out[4 * (o + cnt) + 3] = c < d ? d : c;
+      }
+      ++cnt;
+    }
+  }
+  if (!out) counts[k] = cnt;
+}
+
+inline unsigned nb(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace drops
+}  // namespace tlb
+
+using namespace tlb;
+using namespace tlb::drops;
+
+namespace {
+
+int dfail(lb_handle* h, int code, const char* msg, cudaError_t e = cudaSuccess) {
+  if (h)
+    std::snprintf(h->err, sizeof h->err, "%s%s%s", msg, e != cudaSuccess ? ": " : "",
+                  e != cudaSuccess ? cudaGetErrorString(e) : "");
+  return code;
+}
+
+cudaError_t fields_into(const lb_handle* h, double* stage) {
+  const int pr = h->p.precision;
+  return pr == LB_FP64 ? launch_f64(MODE_FIELDS, h->cfg, h->buf[h->cur], nullptr, stage, h->stream)
+                       : (pr == LB_FP32_SHIFTED ? launch_f32(MODE_FIELDS, h->cfg, h->buf[h->cur], nullptr, stage, h->stream)
+                                                : launch_f32h(MODE_FIELDS, h->cfg, h->buf[h->cur], nullptr, stage, h->stream));
+}
+
+Grid grid_of(const DView& v, const DLayout& L, const lb_params& p) {
+  Grid G;
+  G.cx = v.cx;
+  G.cy = v.cy;
+  G.cstart = v.cstart;
+  G.ccount = v.ccount;
+  G.citems = v.citems;
+  G.ncx = L.ncx;
+  G.ncy = L.ncy;
+  const double wx = (double)p.nx / L.ncx, wy = (double)p.ny / L.ncy;
+  G.cw_min = wx < wy ? wx : wy;
+  return G;
+}
+
+bool check_ws(const lb_handle* h, const void* ws, size_t bytes, int max_drops, DLayout* L) {
+  if (!ws || ((uintptr_t)ws % kAlign) != 0 || max_drops < 1) return false;
+  *L = layout(h->p.nx, h->p.ny, max_drops);
+  return bytes >= L->total;
+}
+
+int read_header(lb_handle* h, const void* ws, Header* out) {
+  const cudaError_t e = cudaMemcpyAsync(out, ws, sizeof(Header), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return dfail(h, LB_ECUDA, "droplet header", e);
+  const cudaError_t e2 = cudaStreamSynchronize(h->stream);
+  if (e2 != cudaSuccess) return dfail(h, LB_ECUDA, "droplet header", e2);
+  return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_droplets_workspace_size(const lb_handle* h, int max_drops, size_t* bytes) {
+  if (!h || !bytes || max_drops < 1) return LB_EINVAL;
+  *bytes = layout(h->p.nx, h->p.ny, max_drops).total;
+  return LB_OK;
+}
+
+int lb_droplets(lb_handle* h, double threshold, int max_drops, void* d_ws, size_t ws_bytes, int* n_drops,
+                int* n_links) {
+  if (!h) return LB_EINVAL;
+  DLayout L;
+  if (!check_ws(h, d_ws, ws_bytes, max_drops, &L))
+    return dfail(h, LB_ENOSPACE, "droplet workspace too small, misaligned or max_drops < 1");
+  if (!(threshold == threshold)) return dfail(h, LB_EINVAL, "threshold is NaN");
+  const DView v = view(d_ws, L);
+  const Geo g{h->p.nx, h->p.ny, h->p.periodic_y, h->cfg.mask};
+  cudaStream_t s = h->stream;
+  const long long N = L.N;
+  double* stage = static_cast<double*>(h->buf[h->cur ^ 1]);  // rho1 is plane 0 of the fields
+  Header hdr{};
+  hdr.max_drops = max_drops;
+  hdr.nx = h->p.nx;
+  hdr.ny = h->p.ny;
+  hdr.periodic_y = h->p.periodic_y;
+  hdr.ncx = L.ncx;
+  hdr.ncy = L.ncy;
+  cudaError_t e = fields_into(h, stage);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v.hdr, &hdr, sizeof hdr, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.cnt, 0, (size_t)max_drops * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.sx, 0, (size_t)max_drops * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.sy, 0, (size_t)max_drops * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.adj, 0xff, (size_t)max_drops * kMaxDeg * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.deg, 0, (size_t)max_drops * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.ccount, 0, (size_t)L.ncell * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.cfill, 0, (size_t)L.ncell * 4, s);
+  if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets", e);
+  const int T = 256;
+  int* err = &v.hdr->err;
+  label_init<<<nb(N, T), T, 0, s>>>(stage, threshold, g, v.lab);
+  label_merge<<<nb(N, T), T, 0, s>>>(g, v.lab, err);
+  label_flatten<<<nb(N, T), T, 0, s>>>(N, v.lab, v.did);
+  e = exclusive_scan(v.did, N, v.did, v.blk, s);  // ids of the roots, in node order
+  if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets scan", e);
+  write_header<<<1, 1, 0, s>>>(v.hdr, v.blk + L.nblk, nullptr, max_drops, 0);
+  label_ids<<<nb(N, T), T, 0, s>>>(N, v.lab, v.did, v.root, max_drops, err);
+  label_ids_spread<<<nb(N, T), T, 0, s>>>(N, v.lab, v.did);
+  e = cudaGetLastError();
+  Header got{};
+  if (e == cudaSuccess) {
+    if (int rc = read_header(h, v.hdr, &got)) return rc;
+  } else {
+    return dfail(h, LB_ECUDA, "lb_droplets labels", e);
+  }
+  if (got.err & kErrUnion) return dfail(h, LB_ECUDA, "droplet labelling did not converge");
+  if (got.err & kErrDrops) return dfail(h, LB_ENOSPACE, "more droplets than max_drops");
+  const int M = got.n_drops;
+  if (M > 0) {
+    centre_sums<<<nb(N, T), T, 0, s>>>(g, v.did, v.root, M, v.cnt, v.sx, v.sy);
+    // cell of each droplet kept in lcount until the links need it
+    centre_final<<<nb(M, T), T, 0, s>>>(g, M, v.root, v.cnt, v.sx, v.sy, v.cx, v.cy, L.ncx, L.ncy, v.ccount, v.lcount);
+    e = exclusive_scan(v.ccount, L.ncell, v.cstart, v.cblk, s);
+    if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets cells", e);
+    cell_fill<<<nb(M, T), T, 0, s>>>(M, v.lcount, v.cstart, v.cfill, v.citems);
+  }
+  const Grid G = grid_of(v, L, h->p);
+  voronoi_colour<<<nb(N, T), T, 0, s>>>(g, G, M, v.col);
+  if (M > 0) {
+    voronoi_links<<<nb(N, T), T, 0, s>>>(g, v.col, v.adj, v.deg, err);
+    adj_sort<<<nb(M, T), T, 0, s>>>(M, v.adj, v.deg, v.lcount);
+    e = exclusive_scan(v.lcount, M, v.loff, v.dblk, s);
+    if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets links", e);
+    links_write<<<nb(M, T), T, 0, s>>>(M, v.adj, v.deg, v.loff, v.links);
+    write_header<<<1, 1, 0, s>>>(v.hdr, nullptr, v.dblk + nb(M, kScanBlock), max_drops, 1);
+  } else {
+    e = cudaMemsetAsync(&v.hdr->n_links, 0, sizeof(int), s);
+    if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets", e);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets", e);
+  if (int rc = read_header(h, v.hdr, &got)) return rc;
+  if (got.err & kErrDegree) return dfail(h, LB_ENOSPACE, "a droplet has more Voronoi neighbours than the adjacency holds");
+  if (n_drops) *n_drops = got.n_drops;
+  if (n_links) *n_links = got.n_links;
+  return LB_OK;
+}
+
+int lb_droplets_get(lb_handle* h, const void* d_ws, size_t ws_bytes, double* cx, double* cy, long long* size,
+                    int* links, int* label, int* color) {
+  if (!h || !d_ws) return LB_EINVAL;
+  Header hd{};
+  if (int rc = read_header(h, d_ws, &hd)) return rc;
+  DLayout L;
+  if (hd.max_drops < 1 || hd.nx != h->p.nx || hd.ny != h->p.ny || !check_ws(h, d_ws, ws_bytes, hd.max_drops, &L))
+    return dfail(h, LB_EINVAL, "workspace does not hold a droplet analysis of this lattice");
+  const DView v = view(const_cast<void*>(d_ws), L);
+  cudaStream_t s = h->stream;
+  const size_t M = (size_t)hd.n_drops, N = (size_t)L.N;
+  cudaError_t e = cudaSuccess;
+  if (cx && M) e = cudaMemcpyAsync(cx, v.cx, M * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && cy && M) e = cudaMemcpyAsync(cy, v.cy, M * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && size && M) e = cudaMemcpyAsync(size, v.cnt, M * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && links && hd.n_links)
+    e = cudaMemcpyAsync(links, v.links, (size_t)hd.n_links * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && label) e = cudaMemcpyAsync(label, v.did, N * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && color) e = cudaMemcpyAsync(color, v.col, N * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets_get", e);
+  return LB_OK;
+}
+
+int lb_droplets_compare(lb_handle* h, const void* d_ws_prev, const void* d_ws_now, size_t ws_bytes, double d_max,
+                        void* d_scratch, size_t scratch_bytes, int* counts4, int* broken, int* arising, int* t1,
+                        int cap) {
+  if (!h || !d_ws_prev || !d_ws_now || !counts4 || !d_scratch || cap < 0) return LB_EINVAL;
+  Header hp{}, hn{};
+  if (int rc = read_header(h, d_ws_prev, &hp)) return rc;
+  if (int rc = read_header(h, d_ws_now, &hn)) return rc;
+  DLayout Lp, Ln;
+  if (hp.max_drops < 1 || hn.max_drops < 1 || hp.nx != h->p.nx || hn.nx != h->p.nx || hp.ny != h->p.ny ||
+      hn.ny != h->p.ny || !check_ws(h, d_ws_prev, ws_bytes, hp.max_drops, &Lp) ||
+      !check_ws(h, d_ws_now, ws_bytes, hn.max_drops, &Ln))
+    return dfail(h, LB_EINVAL, "workspaces do not hold droplet analyses of this lattice");
+  const int Mp = hp.n_drops, Mn = hn.n_drops;
+  // scratch: near_np, n2p (per now droplet), near_pn, p2n (per prev droplet), count / offset / scan
+  // blocks of the broken, arising and T1 lists, and the three lists
+  const int Mx = Mp > Mn ? Mp : Mn;
+  const size_t lmax = (size_t)Mx * kMaxDeg / 2 + 1;
+  unsigned char* sp = static_cast<unsigned char*>(d_scratch);
+  size_t used = 0;
+  auto take = [&](size_t bytes) {
+    int* p = reinterpret_cast<int*>(sp + used);
+    used += round_up(bytes, kAlign);
+    return p;
+  };
+  int* near_np = take((size_t)Mn * 4);
+  int* n2p = take((size_t)Mn * 4);
+  int* near_pn = take((size_t)Mp * 4);
+  int* p2n = take((size_t)Mp * 4);
+  int* cnt[3];
+  int* off[3];
+  int* blk[3];
+  for (int k = 0; k < 3; ++k) {
+    cnt[k] = take((lmax + 1) * 4);
+    off[k] = take((lmax + 1) * 4);
+    blk[k] = take((size_t)(nb((long long)lmax, kScanBlock) + 1) * 4);
+  }
+  int* dbroken = take(lmax * 8);
+  int* darising = take(lmax * 8);
+  int* dt1 = take(lmax * 16);
+  if (scratch_bytes < used || ((uintptr_t)d_scratch % kAlign) != 0) {
+    counts4[0] = (int)((used + 1023) / 1024);  // KiB needed
+    return dfail(h, LB_ENOSPACE, "compare scratch too small or misaligned (counts4[0] = KiB needed)");
+  }
+  const DView vp = view(const_cast<void*>(d_ws_prev), Lp), vn = view(const_cast<void*>(d_ws_now), Ln);
+  const Geo g{h->p.nx, h->p.ny, h->p.periodic_y, h->cfg.mask};
+  const Grid Gp = grid_of(vp, Lp, h->p), Gn = grid_of(vn, Ln, h->p);
+  cudaStream_t s = h->stream;
+  const int T = 256;
+  const double d2max = d_max * d_max;
+  cudaError_t e = cudaMemsetAsync(p2n, 0xff, (size_t)Mp * 4, s);
+  if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets_compare", e);
+  if (Mn > 0) nearest_other<<<nb(Mn, T), T, 0, s>>>(g, Gp, Mn, vn.cx, vn.cy, d2max, near_np);
+  if (Mp > 0) nearest_other<<<nb(Mp, T), T, 0, s>>>(g, Gn, Mp, vp.cx, vp.cy, d2max, near_pn);
+  if (Mn > 0) {
+    mutual<<<nb(Mn, T), T, 0, s>>>(Mn, near_np, near_pn, n2p);
+    invert<<<nb(Mn, T), T, 0, s>>>(Mn, n2p, p2n);
+  }
+  // broken (per prev droplet) and arising (per now droplet): count, scan, write
+  int tot[3] = {0, 0, 0};
+  const int nsrc[2] = {Mp, Mn};
+  for (int mode = 0; mode < 2; ++mode) {
+    const int n = nsrc[mode];
+    if (n == 0) continue;
+    const DView& self = mode == 0 ? vp : vn;
+    const DView& other = mode == 0 ? vn : vp;
+    const int* map = mode == 0 ? p2n : n2p;
+    int* outp = mode == 0 ? dbroken : darising;
+    link_changes<<<nb(n, T), T, 0, s>>>(mode, n, self.adj, self.deg, other.adj, other.deg, map, nullptr, cnt[mode], nullptr);
+    e = exclusive_scan(cnt[mode], n, off[mode], blk[mode], s);
+    if (e == cudaSuccess) {
+      link_changes<<<nb(n, T), T, 0, s>>>(mode, n, self.adj, self.deg, other.adj, other.deg, map, off[mode], nullptr, outp);
+      e = cudaMemcpyAsync(&tot[mode], blk[mode] + nb(n, kScanBlock), sizeof(int), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets_compare", e);
+  }
+  if (tot[0] > 0) {
+    t1_events<<<nb(tot[0], T), T, 0, s>>>(tot[0], dbroken, vp.adj, vp.deg, vn.adj, vn.deg, p2n, nullptr, cnt[2], nullptr);
+    e = exclusive_scan(cnt[2], tot[0], off[2], blk[2], s);
+    if (e == cudaSuccess) {
+      t1_events<<<nb(tot[0], T), T, 0, s>>>(tot[0], dbroken, vp.adj, vp.deg, vn.adj, vn.deg, p2n, off[2], nullptr, dt1);
+      e = cudaMemcpyAsync(&tot[2], blk[2] + nb(tot[0], kScanBlock), sizeof(int), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets_compare t1", e);
+  }
+  // matched count
+  std::vector<int> n2p_h((size_t)Mn);
+  if (Mn > 0) {
+    e = cudaMemcpyAsync(n2p_h.data(), n2p, (size_t)Mn * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets_compare", e);
+  }
+  int matched = 0;
+  for (int j = 0; j < Mn; ++j) matched += n2p_h[j] >= 0 ? 1 : 0;
+  counts4[0] = matched;
+  counts4[1] = tot[0];
+  counts4[2] = tot[1];
+  counts4[3] = tot[2];
+  if (broken && tot[0]) e = cudaMemcpyAsync(broken, dbroken, (size_t)(tot[0] < cap ? tot[0] : cap) * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && arising && tot[1])
+    e = cudaMemcpyAsync(arising, darising, (size_t)(tot[1] < cap ? tot[1] : cap) * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && t1 && tot[2]) e = cudaMemcpyAsync(t1, dt1, (size_t)(tot[2] < cap ? tot[2] : cap) * 16, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets_compare", e);
+  return LB_OK;
+}
+
+}  // extern "C"

@@ -30,7 +30,8 @@ inline const char* check_params(const lb_params* p) {
   if (p->nx < 1 || p->ny < 1) return "nx and ny must be >= 1";
   if ((long long)p->nx * p->ny > (1LL << 31) - 1) return "nx * ny must fit in 31 bits";
   if (!p->periodic_y && p->ny < 3) return "walls (periodic_y = 0) need ny >= 3";
-  if (p->precision != LB_FP64 && p->precision != LB_FP32_SHIFTED) return "precision must be LB_FP64 or LB_FP32_SHIFTED";
+  if (p->precision != LB_FP64 && p->precision != LB_FP32_SHIFTED && p->precision != LB_FP32_FP16T)
+    return "precision must be LB_FP64, LB_FP32_SHIFTED or LB_FP32_FP16T";
   if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return "tau must be finite and > 1/2";
   if (!(p->tau_g > 0.5) || !std::isfinite(p->tau_g)) return "tau_g must be finite and > 1/2";
   if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0)) return "rho0 must be finite and > 0";
@@ -52,7 +53,8 @@ inline Layout layout_for(const lb_params* p, int has_mask) {
   const int per_row = (int)(128 / L.elem);
   L.pitch = (p->nx + per_row - 1) / per_row * per_row;
   const size_t plane = (size_t)L.pitch * p->ny;
-  L.buf_bytes = round_up(27 * plane * L.elem, kAlign);
+  // LB_FP32_FP16T: 18 FP32 fluid planes, then 9 FP16 thermal planes of the same pitch
+  L.buf_bytes = round_up(p->precision == LB_FP32_FP16T ? (18 * 4 + 9 * 2) * plane : 27 * plane * L.elem, kAlign);
   // the inactive buffer doubles as staging for init (3 planes) and fields (5 planes) of doubles
   const size_t staging = (size_t)p->nx * p->ny * 5 * sizeof(double);
   if (staging > L.buf_bytes) L.buf_bytes = round_up(staging, kAlign);
@@ -74,7 +76,7 @@ inline Layout layout_for(const lb_params* p, int has_mask) {
 inline double psi_exp_host(double rho, double rho0) { return rho0 * (1.0 - std::exp(-rho / rho0)); }
 
 // FP64 step constants of one lattice (storage pitch in elements, device mask or nullptr).  The shift
-// constants are used only in FP32-shifted storage.
+// constants are used only in the FP32 storage forms.
 inline StepCfg make_stepcfg(const lb_params& p, int pitch, const uint8_t* d_mask) {
   StepCfg c{};
   c.nx = p.nx;
@@ -104,7 +106,7 @@ inline StepCfg make_stepcfg(const lb_params& p, int pitch, const uint8_t* d_mask
   c.alpha_g = p.alpha_g;
   c.body_fx = p.body_fx;
   c.rho_bar[0] = c.rho_bar[1] = c.T_bar = 0.0;
-  if (p.precision == LB_FP32_SHIFTED) {
+  if (p.precision != LB_FP64) {
     c.rho_bar[0] = p.shift_rho[0];
     c.rho_bar[1] = p.shift_rho[1];
     c.T_bar = p.shift_T;
@@ -139,7 +141,7 @@ inline const char* prepare_fields(lb_params& p, const uint8_t* mask, const doubl
       ++nf;
     }
   if (nf == 0) return "the lattice has no fluid node";
-  if (p.precision == LB_FP32_SHIFTED) {
+  if (p.precision != LB_FP64) {
     if (std::isnan(p.shift_rho[0])) p.shift_rho[0] = sum1 / (double)nf;
     if (std::isnan(p.shift_rho[1])) p.shift_rho[1] = sum2 / (double)nf;
     if (std::isnan(p.shift_T)) p.shift_T = 0.5 * (p.T_down + p.T_up);

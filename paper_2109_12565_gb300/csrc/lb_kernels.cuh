@@ -23,6 +23,7 @@
 // Writes of direction i from a warp land on one contiguous row shifted by
 // c_i; each destination slot has exactly one writer per step.
 #pragma once
+#include <cuda_fp16.h>
 #include <math.h>
 #include <stdint.h>
 
@@ -38,6 +39,40 @@ __host__ __device__ constexpr int cyq(int i) { return (i == 2 || i == 5 || i == 
 __host__ __device__ constexpr int oppq(int i) { return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 5 + 2) % 4) + 5); }
 // D2Q9 weights w_i (Fig. 1b).
 template <class C> __host__ __device__ constexpr C wq(int i) { return i == 0 ? C(4) / C(9) : (i <= 4 ? C(1) / C(9) : C(1) / C(36)); }
+
+// Storage forms.  S = double or float: all 27 planes in S, arithmetic in S.  S = F32H16: the 18
+// fluid planes in FP32 and the 9 thermal planes in FP16 (both as deviations from the shift
+// equilibria), arithmetic in FP32.  A buffer is the 18 fluid planes followed by the 9 thermal planes,
+// each of `plane` elements of its own type.
+struct F32H16 {};
+template <class S> struct Storage {
+  using F = S;  // fluid planes
+  using G = S;  // thermal planes
+  using C = S;  // arithmetic
+};
+template <> struct Storage<F32H16> {
+  using F = float;
+  using G = __half;
+  using C = float;
+};
+template <class S> using SF = typename Storage<S>::F;
+template <class S> using SG = typename Storage<S>::G;
+template <class S> using SC = typename Storage<S>::C;
+
+// First thermal plane of a buffer.
+template <class S> __host__ __device__ __forceinline__ const SG<S>* thermal_planes(const SF<S>* buf, long long plane) {
+  return reinterpret_cast<const SG<S>*>(buf + 18 * plane);
+}
+template <class S> __host__ __device__ __forceinline__ SG<S>* thermal_planes(SF<S>* buf, long long plane) {
+  return reinterpret_cast<SG<S>*>(buf + 18 * plane);
+}
+// Value conversions between storage and arithmetic (round to nearest into FP16).
+template <class C, class T> __device__ __forceinline__ C up(T v) { return C(v); }
+template <> __device__ __forceinline__ float up<float, __half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ double up<double, __half>(__half v) { return (double)__half2float(v); }
+template <class T, class V> __device__ __forceinline__ T down(V v) { return T(v); }
+template <> __device__ __forceinline__ __half down<__half, float>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __half down<__half, double>(double v) { return __double2half(v); }
 
 // Kernel constants in the compute precision C (rounded once on the host).
 template <class C> struct KParams {
@@ -105,10 +140,11 @@ template <bool CG, class S> __device__ __forceinline__ S ld_pop(const S* p) {
 
 // Where phase B reads the populations of its own node: straight from the input buffer.
 template <class S, bool CG> struct GlobalPopSource {
-  const S* __restrict__ fin;
+  const SF<S>* __restrict__ fin;
   int plane;
-  __device__ __forceinline__ S operator()(int k, int idx, int /*tx*/, int /*ty*/) const {
-    return ld_pop<CG>(fin + idx + k * plane);
+  __device__ __forceinline__ SC<S> operator()(int k, int idx, int /*tx*/, int /*ty*/) const {
+    if (k < 18) return up<SC<S>>(ld_pop<CG>(fin + idx + k * plane));
+    return up<SC<S>>(ld_pop<CG>(thermal_planes<S>(fin, plane) + idx + (k - 18) * plane));
   }
 };
 
@@ -148,7 +184,7 @@ template <class C, int TX, int TY, bool NEED_T> struct TileSmem {
 // Phase A on one tile: rho, psi (and T for the observables) on the tile + 2-node ring.
 // Returns (CTA-uniform) whether the fast path applies.
 template <class S, class C, bool SHIFT, bool NEED_T, int TX, int TY, int NT, bool CG>
-__device__ __forceinline__ bool tile_phase_a(const S* __restrict__ fin, const KParams<C>& kp, int x0, int y0,
+__device__ __forceinline__ bool tile_phase_a(const SF<S>* __restrict__ fin, const KParams<C>& kp, int x0, int y0,
                                              TileSmem<C, TX, TY, NEED_T>& sm, int tid) {
   constexpr int RX = TX + 4, RY = TY + 4;
   const int nx = kp.nx, ny = kp.ny, pitch = kp.pitch, plane = kp.plane;
@@ -178,7 +214,7 @@ __device__ __forceinline__ bool tile_phase_a(const S* __restrict__ fin, const KP
       if constexpr (NEED_T) sm.T[ry][rx] = (2 * gy < ny) ? kp.T_down : kp.T_up;
       sm.solid[ry][rx] = 1;
     } else {
-      const S* src = fin + (gy * pitch + gx);
+      const SF<S>* src = fin + (gy * pitch + gx);
       C f[9], h[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
@@ -201,8 +237,9 @@ __device__ __forceinline__ bool tile_phase_a(const S* __restrict__ fin, const KP
       }
       if constexpr (NEED_T) {
         C t = C(0);
+        const SG<S>* tsrc = thermal_planes<S>(fin, plane) + (gy * pitch + gx);  // node offset in thermal elements
 #pragma unroll
-        for (int i = 0; i < 9; ++i) t += C(ld_pop<CG>(src + (18 + i) * plane));
+        for (int i = 0; i < 9; ++i) t += up<C>(ld_pop<CG>(tsrc + i * plane));
         sm.T[ry][rx] = t + (SHIFT ? kp.T_bar : C(0));
       }
       sm.solid[ry][rx] = 0;
@@ -217,10 +254,11 @@ __device__ __forceinline__ bool tile_phase_a(const S* __restrict__ fin, const KP
 // Interaction + external forces at the node whose shared-memory centre is (cx, cy), with the parts
 // the adjoint needs: the cross stencil sum cr = sum_NN w_i rho_m(x + c_i) c_i, the self stencil sum
 // s = sum_24 (G^a w_i + G^r p_i) psi_l(x + c_i) c_i and psi_l(x).
-template <class C, int TX, int TY, bool NEED_T>
-__device__ __forceinline__ void node_force_parts(const TileSmem<C, TX, TY, NEED_T>& sm, const KParams<C>& kp, int cx,
-                                                 int cy, C r1, C r2, C T, C Fx[2], C Fy[2], C crx[2], C cry[2],
-                                                 C sx[2], C sy[2], C psl[2]) {
+// SM is any shared-memory view with rho[2][rows][cols] and psi[2][rows][cols] (the tile of the fused
+// step, the row window of the strip-marching step).
+template <class C, class SM>
+__device__ __forceinline__ void node_force_parts(const SM& sm, const KParams<C>& kp, int cx, int cy, C r1, C r2, C T,
+                                                 C Fx[2], C Fy[2], C crx[2], C cry[2], C sx[2], C sy[2], C psl[2]) {
 #pragma unroll
   for (int l = 0; l < 2; ++l) {
     const int m = 1 - l;
@@ -257,11 +295,11 @@ __device__ __forceinline__ void node_force_parts(const TileSmem<C, TX, TY, NEED_
   }
 }
 
-template <class C, int TX, int TY, bool NEED_T>
-__device__ __forceinline__ void node_forces(const TileSmem<C, TX, TY, NEED_T>& sm, const KParams<C>& kp, int cx, int cy,
-                                            C r1, C r2, C T, C Fx[2], C Fy[2]) {
+template <class C, class SM>
+__device__ __forceinline__ void node_forces(const SM& sm, const KParams<C>& kp, int cx, int cy, C r1, C r2, C T,
+                                            C Fx[2], C Fy[2]) {
   C crx[2], cry[2], sx[2], sy[2], psl[2];
-  node_force_parts<C, TX, TY, NEED_T>(sm, kp, cx, cy, r1, r2, T, Fx, Fy, crx, cry, sx, sy, psl);
+  node_force_parts<C, SM>(sm, kp, cx, cy, r1, r2, T, Fx, Fy, crx, cry, sx, sy, psl);
 }
 
 // Reciprocals of rho_1, rho_2 and rho_1 + rho_2 from one division.
@@ -327,10 +365,54 @@ __device__ __forceinline__ void node_collide(const KParams<C>& kp, const C f[9],
     collide_thermal<C, SHIFT, true>(kp, g, T, dT, uHx, uHy, post);
 }
 
+// Streaming (push) of the 27 post-collision populations of fluid node (gx, gy) (row-major index idx in
+// the padded buffer) with half-way bounce-back of f and thermal anti-bounce-back of g where x + c_i is
+// solid (Sec. 2.2).  solid[cy + c_iy][cx + c_ix] is the solid flag of x + c_i in the caller's
+// shared-memory view.  FAST: no solid node around and no periodic wrap, every store is a constant offset.
+template <class S, class C, bool FAST, int RX>
+__device__ __forceinline__ void push_store(SF<S>* __restrict__ fout, const KParams<C>& kp, int idx, int gx, int gy,
+                                           const C post[27], const unsigned char (*solid)[RX], int cx, int cy) {
+  using F = SF<S>;
+  using G = SG<S>;
+  const int nx = kp.nx, ny = kp.ny, pitch = kp.pitch, plane = kp.plane;
+  G* __restrict__ gout = thermal_planes<S>(fout, plane);
+  if constexpr (FAST) {
+    F* dst = fout + idx;
+    G* gdst = gout + idx;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int off = cxq(i) + cyq(i) * pitch;
+      dst[i * plane + off] = down<F>(post[i]);
+      dst[(9 + i) * plane + off] = down<F>(post[9 + i]);
+      gdst[i * plane + off] = down<G>(post[18 + i]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      if (!solid[cy + cyq(i)][cx + cxq(i)]) {
+        int dx = gx + cxq(i);
+        dx = dx < 0 ? dx + nx : (dx >= nx ? dx - nx : dx);
+        int dy = gy + cyq(i);
+        if (kp.periodic_y) dy = dy < 0 ? dy + ny : (dy >= ny ? dy - ny : dy);
+        const int didx = dy * pitch + dx;
+        fout[i * plane + didx] = down<F>(post[i]);
+        fout[(9 + i) * plane + didx] = down<F>(post[9 + i]);
+        gout[i * plane + didx] = down<G>(post[18 + i]);
+      } else {
+        const int o = oppq(i);
+        const C twoTw = (2 * (gy + cyq(i)) < ny) ? kp.twoTw_down : kp.twoTw_up;
+        fout[o * plane + idx] = down<F>(post[i]);
+        fout[(9 + o) * plane + idx] = down<F>(post[9 + i]);
+        gout[o * plane + idx] = down<G>(-post[18 + i] + wq<C>(i) * twoTw);
+      }
+    }
+  }
+}
+
 // Phase B on one tile.  MODE_STEP: collide and push-store; MODE_OBS: accumulate the observables
 // of the node into acc[]; MODE_FIELDS: write rho1, rho2, T, u^(H) to aux planes.
 template <class S, class C, bool SHIFT, int MODE, bool FAST, int TX, int TY, int BY, class Src>
-__device__ __forceinline__ void tile_phase_b(const Src& pop, S* __restrict__ fout, const KParams<C>& kp, int x0, int y0,
+__device__ __forceinline__ void tile_phase_b(const Src& pop, SF<S>* __restrict__ fout, const KParams<C>& kp, int x0, int y0,
                                              const TileSmem<C, TX, TY, MODE != MODE_STEP>& sm, double* __restrict__ aux,
                                              double acc[kObsSlots]) {
   const int nx = kp.nx, ny = kp.ny, pitch = kp.pitch, plane = kp.plane;
@@ -374,7 +456,7 @@ __device__ __forceinline__ void tile_phase_b(const Src& pop, S* __restrict__ fou
     const C T = dT + Tb;
     const C jx = sm.jx[ty][tx], jy = sm.jy[ty][tx];
     C Fx[2], Fy[2];
-    node_forces<C, TX, TY, MODE != MODE_STEP>(sm, kp, cx, cy, r1, r2, T, Fx, Fy);
+    node_forces<C>(sm, kp, cx, cy, r1, r2, T, Fx, Fy);
     // velocities: Eq. velo, Eq. shift, u^(H) = u + F / (2 rho)
     C i1, i2, inv_rho;
     three_reciprocals<C>(r1, r2, i1, i2, inv_rho);
@@ -407,44 +489,14 @@ __device__ __forceinline__ void tile_phase_b(const Src& pop, S* __restrict__ fou
     } else {
       C post[27];
       node_collide<C, SHIFT>(kp, f, h, g, r1, r2, dr1, dr2, T, dT, ux, uy, i1, i2, Fx, Fy, uHx, uHy, post);
-      // streaming (push) with half-way bounce-back / thermal anti-bounce-back
-      if constexpr (FAST) {
-        S* dst = fout + idx;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          const int off = cxq(i) + cyq(i) * pitch;
-          dst[i * plane + off] = S(post[i]);
-          dst[(9 + i) * plane + off] = S(post[9 + i]);
-          dst[(18 + i) * plane + off] = S(post[18 + i]);
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          if (!sm.solid[cy + cyq(i)][cx + cxq(i)]) {
-            int dx = gx + cxq(i);
-            dx = dx < 0 ? dx + nx : (dx >= nx ? dx - nx : dx);
-            int dy = gy + cyq(i);
-            if (kp.periodic_y) dy = dy < 0 ? dy + ny : (dy >= ny ? dy - ny : dy);
-            const int didx = dy * pitch + dx;
-            fout[i * plane + didx] = S(post[i]);
-            fout[(9 + i) * plane + didx] = S(post[9 + i]);
-            fout[(18 + i) * plane + didx] = S(post[18 + i]);
-          } else {
-            const int o = oppq(i);
-            const C twoTw = (2 * (gy + cyq(i)) < ny) ? kp.twoTw_down : kp.twoTw_up;
-            fout[o * plane + idx] = S(post[i]);
-            fout[(9 + o) * plane + idx] = S(post[9 + i]);
-            fout[(18 + o) * plane + idx] = S(-post[18 + i] + wq<C>(i) * twoTw);
-          }
-        }
-      }
+      push_store<S, C, FAST>(fout, kp, idx, gx, gy, post, sm.solid, cx, cy);
     }
   }
 }
 
 // One tile: phase A, barrier, phase B (fast path when the CTA allows it).
 template <class S, class C, bool SHIFT, int MODE, int TX, int TY, int BY, bool CG = false>
-__device__ __forceinline__ void tile_step(const S* __restrict__ fin, S* __restrict__ fout, const KParams<C>& kp,
+__device__ __forceinline__ void tile_step(const SF<S>* __restrict__ fin, SF<S>* __restrict__ fout, const KParams<C>& kp,
                                           int x0, int y0, TileSmem<C, TX, TY, MODE != MODE_STEP>& sm,
                                           double* __restrict__ aux, double acc[kObsSlots]) {
   constexpr int NT = TX * BY;
@@ -478,7 +530,7 @@ __device__ __forceinline__ void block_obs_store(double acc[kObsSlots], double* _
 
 template <class S, class C, bool SHIFT, int MODE, int TX, int TY, int BY, int MINB>
 __global__ void __launch_bounds__(TX * BY, MINB)
-lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const KParams<C> kp, double* __restrict__ aux) {
+lb_step_kernel(const SF<S>* __restrict__ fin, SF<S>* __restrict__ fout, const KParams<C> kp, double* __restrict__ aux) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto& sm = *reinterpret_cast<TileSmem<C, TX, TY, MODE != MODE_STEP>*>(smem_raw);
   double acc[kObsSlots];
@@ -490,7 +542,7 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const KParams<C>
 
 // Rest equilibria f = w_i rho, g = w_i T at fluid nodes (stored minus the shift), 0 at solid nodes.
 template <class S, bool SHIFT>
-__global__ void lb_init_kernel(const double* __restrict__ fields, S* __restrict__ buf, const StepCfg cfg) {
+__global__ void lb_init_kernel(const double* __restrict__ fields, SF<S>* __restrict__ buf, const StepCfg cfg) {
   const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
   if (gx >= cfg.nx || gy >= cfg.ny) return;
   const long long n = (long long)gy * cfg.nx + gx, N = (long long)cfg.nx * cfg.ny;
@@ -506,9 +558,9 @@ __global__ void lb_init_kernel(const double* __restrict__ fields, S* __restrict_
       b = w * (r2 - cfg.rho_bar[1]);
       c = w * (T - cfg.T_bar);
     }
-    buf[i * cfg.plane + idx] = solid ? S(0) : S(a);
-    buf[(9 + i) * cfg.plane + idx] = solid ? S(0) : S(b);
-    buf[(18 + i) * cfg.plane + idx] = solid ? S(0) : S(c);
+    buf[i * cfg.plane + idx] = down<SF<S>>(solid ? 0.0 : a);
+    buf[(9 + i) * cfg.plane + idx] = down<SF<S>>(solid ? 0.0 : b);
+    thermal_planes<S>(buf, cfg.plane)[i * cfg.plane + idx] = down<SG<S>>(solid ? 0.0 : c);
   }
 }
 
@@ -519,34 +571,40 @@ __device__ __forceinline__ double shift_of(const StepCfg& cfg, int k) {
 }
 
 template <class S, bool SHIFT>
-__global__ void lb_plane_get_kernel(int k, const S* __restrict__ buf, double* __restrict__ out, const StepCfg cfg) {
+__global__ void lb_plane_get_kernel(int k, const SF<S>* __restrict__ buf, double* __restrict__ out, const StepCfg cfg) {
   const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
   if (gx >= cfg.nx || gy >= cfg.ny) return;
   const long long n = (long long)gy * cfg.nx + gx;
   bool solid = cfg.mask != nullptr && cfg.mask[n] != 0;
   if (!cfg.periodic_y && (gy == 0 || gy == cfg.ny - 1)) solid = true;
-  const double v = (double)buf[k * cfg.plane + (long long)gy * cfg.pitch + gx];
+  const long long idx = (long long)gy * cfg.pitch + gx;
+  const double v = k < 18 ? up<double>(buf[k * cfg.plane + idx])
+                          : up<double>(thermal_planes<S>(buf, cfg.plane)[(k - 18) * cfg.plane + idx]);
   out[n] = solid ? 0.0 : (SHIFT ? v + shift_of(cfg, k) : v);
 }
 
 template <class S, bool SHIFT>
-__global__ void lb_plane_put_kernel(int k, const double* __restrict__ in, S* __restrict__ buf, const StepCfg cfg) {
+__global__ void lb_plane_put_kernel(int k, const double* __restrict__ in, SF<S>* __restrict__ buf, const StepCfg cfg) {
   const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
   if (gx >= cfg.nx || gy >= cfg.ny) return;
   const long long n = (long long)gy * cfg.nx + gx;
   bool solid = cfg.mask != nullptr && cfg.mask[n] != 0;
   if (!cfg.periodic_y && (gy == 0 || gy == cfg.ny - 1)) solid = true;
   const double v = SHIFT ? in[n] - shift_of(cfg, k) : in[n];
-  buf[k * cfg.plane + (long long)gy * cfg.pitch + gx] = solid ? S(0) : S(v);
+  const long long idx = (long long)gy * cfg.pitch + gx;
+  if (k < 18)
+    buf[k * cfg.plane + idx] = down<SF<S>>(solid ? 0.0 : v);
+  else
+    thermal_planes<S>(buf, cfg.plane)[(k - 18) * cfg.plane + idx] = down<SG<S>>(solid ? 0.0 : v);
 }
 
 // Launch with the tile's shared memory as dynamic shared memory (the larger tiles need more than
 // the 48 KB static limit); the opt-in attribute is set once per kernel instantiation.
 template <class S, int MODE, int TX, int TY, int BY, int MB, bool SHIFT>
-cudaError_t launch_tile_kernel(const dim3& grid, const S* in, S* out, const KParams<S>& kp, double* aux,
+cudaError_t launch_tile_kernel(const dim3& grid, const SF<S>* in, SF<S>* out, const KParams<SC<S>>& kp, double* aux,
                                cudaStream_t s) {
-  constexpr size_t bytes = sizeof(TileSmem<S, TX, TY, MODE != MODE_STEP>);
-  auto kern = lb_step_kernel<S, S, SHIFT, MODE, TX, TY, BY, MB>;
+  constexpr size_t bytes = sizeof(TileSmem<SC<S>, TX, TY, MODE != MODE_STEP>);
+  auto kern = lb_step_kernel<S, SC<S>, SHIFT, MODE, TX, TY, BY, MB>;
   static std::atomic<unsigned long long> done{0};  // one bit per device ordinal (mod 64)
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -567,12 +625,13 @@ template <> struct MinBlocks<float> { static constexpr int value = 3; };
 
 template <class S, bool SHIFT>
 cudaError_t launch_impl(int mode, const StepCfg& c, const void* fin, void* fout, double* aux, cudaStream_t s) {
-  using T = Tile<S>;
-  constexpr int MB = MinBlocks<S>::value;
+  using C = SC<S>;
+  using T = Tile<C>;
+  constexpr int MB = MinBlocks<C>::value;
   const dim3 grid = grid_for(c.nx, c.ny, T::TX, T::TY);
-  const S* in = static_cast<const S*>(fin);
-  S* out = static_cast<S*>(fout);
-  const KParams<S> kp = make_kparams<S>(c);
+  const SF<S>* in = static_cast<const SF<S>*>(fin);
+  SF<S>* out = static_cast<SF<S>*>(fout);
+  const KParams<C> kp = make_kparams<C>(c);
   switch (mode) {
     case MODE_STEP:
       return launch_tile_kernel<S, MODE_STEP, T::TX, T::TY, T::BY, MB, SHIFT>(grid, in, out, kp, aux, s);
@@ -587,8 +646,9 @@ cudaError_t launch_impl(int mode, const StepCfg& c, const void* fin, void* fout,
 
 template <class S, bool SHIFT, int TX, int TY, int BY, int MB>
 cudaError_t launch_step_shape(const StepCfg& c, const void* fin, void* fout, cudaStream_t s) {
-  return launch_tile_kernel<S, MODE_STEP, TX, TY, BY, MB, SHIFT>(grid_for(c.nx, c.ny, TX, TY), static_cast<const S*>(fin),
-                                                               static_cast<S*>(fout), make_kparams<S>(c), nullptr, s);
+  return launch_tile_kernel<S, MODE_STEP, TX, TY, BY, MB, SHIFT>(grid_for(c.nx, c.ny, TX, TY),
+                                                               static_cast<const SF<S>*>(fin), static_cast<SF<S>*>(fout),
+                                                               make_kparams<SC<S>>(c), nullptr, s);
 }
 
 inline dim3 rows_grid(const StepCfg& c) { return dim3((unsigned)((c.nx + 127) / 128), (unsigned)c.ny, 1u); }

@@ -19,7 +19,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
-#include "lb_kernels.cuh"
+#include "lb_tma_util.cuh"
 
 namespace tlb {
 
@@ -33,44 +33,6 @@ template <int TX, int TY, int STAGES> struct alignas(128) TmaSmem {
   TileSmem<float, TX, TY, false> t;
   unsigned long long bar[STAGES];
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, unsigned long long* bar, int x, int y,
-                                            int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
-          smem_u32(dst)),
-      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
-
-// Bounded wait of one stage; false when the SM-clock budget ran out.
-__device__ __forceinline__ bool stage_wait(unsigned long long* bar, uint32_t parity, long long budget) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > budget) return false;
-  return true;
-}
 
 // Phase B source: the tile's own populations from the shared-memory stage.
 template <int TX, int TY> struct StagePopSource {
@@ -211,35 +173,7 @@ lb_step_tma_kernel(const __grid_constant__ CUtensorMap map_fluid, const __grid_c
 namespace {
 
 using tlb::TileChoice;
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encoder() {
-  static EncodeTiledFn fn = [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      return (EncodeTiledFn) nullptr;
-    return reinterpret_cast<EncodeTiledFn>(p);
-  }();
-  return fn;
-}
-
-// 3-D view (x, y, plane) of a 27-plane FP32 buffer with a (bx, by, bz) box.
-bool make_map(CUtensorMap* m, const tlb::StepCfg& c, const void* buf, int bx, int by, int bz) {
-  EncodeTiledFn enc = encoder();
-  if (!enc) return false;
-  const cuuint64_t dims[3] = {(cuuint64_t)c.nx, (cuuint64_t)c.ny, 27};
-  const cuuint64_t strides[2] = {(cuuint64_t)c.pitch * 4, (cuuint64_t)c.plane * 4};
-  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(buf), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
+using tlb_tma_host::make_map;
 
 template <int TX, int TY, int BY, int STAGES>
 cudaError_t launch_tma(const tlb::StepCfg& c, const void* fin, void* fout, cudaStream_t s) {

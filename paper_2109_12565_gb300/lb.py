@@ -15,16 +15,17 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtlbgb300.so")
 
 LB_OK, LB_EINVAL, LB_ENOSPACE, LB_ECUDA, LB_ETIMEOUT, LB_EUNSTABLE = 0, -1, -2, -3, -4, -5
-LB_FP64, LB_FP32_SHIFTED = 0, 1
+LB_FP64, LB_FP32_SHIFTED, LB_FP32_FP16T = 0, 1, 2
 _NAMES = {0: "LB_OK", -1: "LB_EINVAL", -2: "LB_ENOSPACE", -3: "LB_ECUDA", -4: "LB_ETIMEOUT", -5: "LB_EUNSTABLE"}
 
 # every symbol include/tlb.h declares
 EXPORTS = ("lb_workspace_size", "lb_init", "lb_step", "lb_observables", "lb_get_fields", "lb_get_state",
-           "lb_set_state", "lb_sync", "lb_destroy", "lb_last_error", "lb_version", "lb_autotune", "lb_set_tile",
-           "lb_tile_info", "lb_batch_workspace_size", "lb_batch_init", "lb_batch_step", "lb_batch_configure",
+           "lb_set_state", "lb_sync", "lb_destroy", "lb_last_error", "lb_version", "lb_autotune", "lb_autotune_cold",
+           "lb_set_tile", "lb_tile_info", "lb_batch_workspace_size", "lb_batch_init", "lb_batch_step", "lb_batch_configure",
            "lb_batch_autotune", "lb_batch_info", "lb_batch_observables", "lb_batch_get_fields", "lb_batch_get_state",
            "lb_batch_sync", "lb_batch_set_wait_budget", "lb_batch_destroy", "lb_batch_last_error",
-           "lb_state_layout", "lb_adjoint_workspace_size", "lb_adjoint_step", "lb_adjoint", "lb_adjoint_timing")
+           "lb_state_layout", "lb_adjoint_workspace_size", "lb_adjoint_step", "lb_adjoint", "lb_adjoint_timing",
+           "lb_droplets_workspace_size", "lb_droplets", "lb_droplets_get", "lb_droplets_compare")
 
 
 class LbError(RuntimeError):
@@ -76,6 +77,7 @@ def lib():
         L.lb_last_error.argtypes = [vp]
         L.lb_last_error.restype = ctypes.c_char_p
         L.lb_autotune.argtypes = [vp, i, ctypes.POINTER(i), dp, i]
+        L.lb_autotune_cold.argtypes = [vp, i, vp, sz, ctypes.POINTER(i), dp, i]
         L.lb_set_tile.argtypes = [vp, i]
         L.lb_tile_info.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
         ip, ll = ctypes.POINTER(ctypes.c_int), ctypes.c_longlong
@@ -106,10 +108,18 @@ def lib():
         L.lb_adjoint_timing.argtypes = [dp]
         for f in ("lb_state_layout", "lb_adjoint_workspace_size", "lb_adjoint_step", "lb_adjoint", "lb_adjoint_timing"):
             getattr(L, f).restype = ctypes.c_int
+        L.lb_droplets_workspace_size.argtypes = [vp, i, ctypes.POINTER(sz)]
+        L.lb_droplets.argtypes = [vp, ctypes.c_double, i, vp, sz, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.lb_droplets_get.argtypes = [vp, vp, sz, dp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(i),
+                                      ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.lb_droplets_compare.argtypes = [vp, vp, vp, sz, ctypes.c_double, vp, sz, ctypes.POINTER(i),
+                                          ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), i]
+        for f in ("lb_droplets_workspace_size", "lb_droplets", "lb_droplets_get", "lb_droplets_compare"):
+            getattr(L, f).restype = ctypes.c_int
         L.lb_version.argtypes = []
         L.lb_version.restype = ctypes.c_char_p
         for f in ("lb_workspace_size", "lb_init", "lb_step", "lb_observables", "lb_get_fields", "lb_get_state",
-                  "lb_set_state", "lb_sync", "lb_autotune", "lb_set_tile", "lb_tile_info"):
+                  "lb_set_state", "lb_sync", "lb_autotune", "lb_autotune_cold", "lb_set_tile", "lb_tile_info"):
             getattr(L, f).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -174,6 +184,21 @@ class Lattice:
                              _dp(self._t0), ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
                              ctypes.c_void_p(self.stream.cuda_stream)))
 
+    @classmethod
+    def from_state(cls, params, state, mask=None, precision=LB_FP64, device=None, stream=None):
+        """A lattice whose S_0 is a given state (27 planes of ny x nx doubles): the restart of a run
+        under new parameters, e.g. a prepared emulsion continued with buoyancy.  The lattice is
+        created from the state's own moments (which also fix the FP32 shifts) and then loaded with
+        lb_set_state; the step counter starts at 0."""
+        st = np.ascontiguousarray(state, dtype=np.float64)
+        rho1, rho2, T = st[0:9].sum(axis=0), st[9:18].sum(axis=0), st[18:27].sum(axis=0)
+        # solid nodes hold 0; any positive density will do there (lb_init ignores them)
+        rho1 = np.where(rho1 > 0.0, rho1, 1.0)
+        rho2 = np.where(rho2 > 0.0, rho2, 1.0)
+        g = cls(params, rho1, rho2, T, mask=mask, precision=precision, device=device, stream=stream)
+        g.set_state(st)
+        return g
+
     # -- C-ABI calls
     def step(self, n=1):
         _check(lib().lb_step(self._h, int(n)), self._h)
@@ -210,13 +235,82 @@ class Lattice:
             _check(n, self._h)
         return {"tx": tx.value, "ty": ty.value, "threads": th.value, "candidates": n}
 
-    def autotune(self, launches=20):
-        """Time every tile candidate (state unchanged) and keep the fastest; returns (index, ms list)."""
+    def autotune(self, launches=20, scratch=None):
+        """Time every tile candidate (state unchanged) and keep the fastest; returns (index, ms list).
+
+        With ``scratch`` (a device tensor larger than L2, overwritten) every timed launch starts with
+        the state evicted from L2 (lb_autotune_cold); without it the launches run back to back."""
         n = self.tile_info(0)["candidates"]
         ms = np.zeros(n)
         chosen = ctypes.c_int()
-        _check(lib().lb_autotune(self._h, int(launches), ctypes.byref(chosen), _dp(ms), n), self._h)
+        if scratch is None:
+            _check(lib().lb_autotune(self._h, int(launches), ctypes.byref(chosen), _dp(ms), n), self._h)
+        else:
+            nbytes = scratch.numel() * scratch.element_size()
+            _check(lib().lb_autotune_cold(self._h, int(launches), ctypes.c_void_p(scratch.data_ptr()), nbytes,
+                                          ctypes.byref(chosen), _dp(ms), n), self._h)
         return chosen.value, ms.tolist()
+
+    # -- droplet topology (lb_droplets*)
+    def droplets(self, threshold=0.8, max_drops=None, arrays=True):
+        """Droplet analysis of the current state (labels, centres, digital Voronoi, links).  Returns a
+        dict with the counts and, with arrays=True, the host copies; the device workspace is kept
+        in the dict ("ws") for droplet_t1."""
+        import torch
+
+        if max_drops is None:
+            max_drops = max(16, self.nx * self.ny // 64)
+        n = ctypes.c_size_t()
+        _check(lib().lb_droplets_workspace_size(self._h, int(max_drops), ctypes.byref(n)), self._h)
+        ws = torch.empty(n.value, dtype=torch.uint8, device=self.workspace.device)
+        M, K = ctypes.c_int(), ctypes.c_int()
+        _check(lib().lb_droplets(self._h, float(threshold), int(max_drops), ctypes.c_void_p(ws.data_ptr()), n.value,
+                                 ctypes.byref(M), ctypes.byref(K)), self._h)
+        out = {"n": M.value, "n_links": K.value, "ws": ws, "ws_bytes": n.value}
+        if arrays:
+            m, k = max(M.value, 1), max(K.value, 1)
+            cx, cy = np.zeros(m), np.zeros(m)
+            size = np.zeros(m, dtype=np.int64)
+            links = np.zeros((k, 2), dtype=np.int32)
+            label = np.zeros((self.ny, self.nx), dtype=np.int32)
+            color = np.zeros((self.ny, self.nx), dtype=np.int32)
+            ip = ctypes.POINTER(ctypes.c_int)
+            _check(lib().lb_droplets_get(self._h, ctypes.c_void_p(ws.data_ptr()), n.value, _dp(cx), _dp(cy),
+                                         size.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                         links.ctypes.data_as(ip), label.ctypes.data_as(ip),
+                                         color.ctypes.data_as(ip)), self._h)
+            out.update(cx=cx[:M.value], cy=cy[:M.value], size=size[:M.value], links=links[:K.value], label=label,
+                       color=color)
+        return out
+
+    def droplet_t1(self, prev, now, d_max, cap=None):
+        """T1 events between two results of droplets() (lb_droplets_compare)."""
+        import torch
+
+        if prev["ws_bytes"] != now["ws_bytes"]:
+            raise ValueError("both analyses need the same max_drops")
+        cap = int(cap if cap is not None else 16 * max(prev["n"], now["n"], 1))
+        counts = (ctypes.c_int * 4)()
+        ip = ctypes.POINTER(ctypes.c_int)
+        scratch_bytes = 1 << 20
+        for _ in range(2):
+            scratch = torch.empty(scratch_bytes, dtype=torch.uint8, device=self.workspace.device)
+            broken = np.zeros((max(cap, 1), 2), dtype=np.int32)
+            arising = np.zeros((max(cap, 1), 2), dtype=np.int32)
+            t1 = np.zeros((max(cap, 1), 4), dtype=np.int32)
+            rc = lib().lb_droplets_compare(self._h, ctypes.c_void_p(prev["ws"].data_ptr()),
+                                           ctypes.c_void_p(now["ws"].data_ptr()), now["ws_bytes"], float(d_max),
+                                           ctypes.c_void_p(scratch.data_ptr()), scratch_bytes, counts,
+                                           broken.ctypes.data_as(ip), arising.ctypes.data_as(ip),
+                                           t1.ctypes.data_as(ip), cap)
+            if rc == LB_ENOSPACE:
+                scratch_bytes = int(counts[0]) * 1024 + 4096
+                continue
+            _check(rc, self._h)
+            break
+        nb_, na_, nt_ = (min(int(counts[k]), cap) for k in (1, 2, 3))
+        return {"matched": int(counts[0]), "n_broken": int(counts[1]), "n_arising": int(counts[2]),
+                "n_t1": int(counts[3]), "broken": broken[:nb_], "arising": arising[:na_], "t1": t1[:nt_]}
 
     def set_tile(self, candidate):
         _check(lib().lb_set_tile(self._h, int(candidate)), self._h)

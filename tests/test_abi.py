@@ -51,6 +51,10 @@ def test_workspace_size_layout():
     assert lb.workspace_size(w.params, True, lb.LB_FP64) > n64
     big = I.emulsion_1024x512()
     assert lb.workspace_size(big.params, False, lb.LB_FP64) < 2 * 27 * 1024 * 512 * 8 * 1.01
+    # FP32 fluid + FP16 thermal: 18 * 4 + 9 * 2 = 90 bytes per node and buffer
+    n16 = lb.workspace_size(big.params, False, lb.LB_FP32_FP16T)
+    assert 2 * 90 * 1024 * 512 <= n16 < 2 * 90 * 1024 * 512 * 1.01
+    assert n16 < lb.workspace_size(big.params, False, lb.LB_FP32_SHIFTED)
 
 
 @pytest.mark.parametrize("bad", [dict(tau=0.5), dict(tau_g=0.4), dict(rho0=0.0), dict(nx=0), dict(ny=2),

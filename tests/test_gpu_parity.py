@@ -17,6 +17,10 @@ from paper_2109_12565_gb300 import lb
 
 pytestmark = pytest.mark.gpu
 
+# FP32 fluid + FP16 thermal: tolerances on T (norm-relative, 200 steps) and on the time-averaged Nu
+FP16T_T_TOL = 3e-3
+FP16T_NU_TOL = 1e-3
+
 
 @pytest.fixture(scope="module", autouse=True)
 def _built():
@@ -155,6 +159,58 @@ def test_fp32_shifted_against_fp64_oracle_200_steps():
     np.testing.assert_allclose(g.observables()["mass"], o.observables()["mass"], rtol=1e-6)
 
 
+def test_fp16_thermal_against_fp64_oracle_200_steps():
+    """FP32 fluid + FP16 thermal storage: every step rounds the thermal deviations g_i - w_i T_bar to
+    FP16 (relative half-ulp 2^-11), so T carries a rounding noise of at most 2^-11 sum_i |g_i - w_i T_bar|
+    <= 2^-11 |T - T_bar| ~ 2.4e-4 per step at |T - T_bar| <= 1/2, which diffusion damps; rho sees T
+    only through the buoyancy alpha_g T and keeps the FP32 bound."""
+    w = I.emulsion_small()
+    g, o = _pair(w.params, w.rho1, w.rho2, w.T0, precision=lb.LB_FP32_FP16T)
+    nu_g, nu_o = [], []
+    for _ in range(200):
+        g.step(1)
+        o.step(1)
+        nu_g.append(g.observables()["Nu"])
+        nu_o.append(o.observables()["Nu"])
+    fg, fo = g.fields(), o.fields()
+    for k in ("rho1", "rho2"):
+        assert _norm_rel(fg[k], fo[k]) <= 1e-4, (k, _norm_rel(fg[k], fo[k]))
+    assert _norm_rel(fg["T"], fo["T"]) <= FP16T_T_TOL, _norm_rel(fg["T"], fo["T"])
+    assert abs(np.mean(nu_g) - np.mean(nu_o)) <= FP16T_NU_TOL * abs(np.mean(nu_o))
+    np.testing.assert_allclose(g.observables()["mass"], o.observables()["mass"], rtol=1e-6)
+
+
+def test_fp16_thermal_state_roundtrip():
+    """Set/get of the state rounds g_i - w_i T_bar to FP16 once (relative half-ulp 2^-11) and keeps the
+    fluid planes at FP32."""
+    w = I.emulsion_small()
+    g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, precision=lb.LB_FP32_FP16T)
+    o = O.Oracle(w.params, w.rho1, w.rho2, w.T0)
+    wts = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    T_bar = 0.5 * (w.params["T_down"] + w.params["T_up"])
+    solid = o.solid().astype(bool)
+    dev = o.state[18:] - wts[:, None, None] * T_bar
+    dev[:, solid] = 0.0
+    bound = 2.0 ** -11 * np.abs(dev) + 1e-12
+    for st in (g.get_state(), None):
+        if st is None:
+            g.set_state(o.state)
+            st = g.get_state()
+        assert np.abs(st[:18] - o.state[:18]).max() <= 1e-7
+        assert np.all(np.abs(st[18:] - o.state[18:]) <= bound)
+
+
+def test_fp16_thermal_rejected_by_batch_and_adjoint():
+    w = I.emulsion_small(nx=32, ny=16, n_drops=1, R=4.0)
+    with pytest.raises(lb.LbError) as e:
+        lb.batch_workspace_size([w.params], precision=lb.LB_FP32_FP16T)
+    assert e.value.code == lb.LB_EINVAL
+    g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, precision=lb.LB_FP32_FP16T)
+    with pytest.raises(lb.LbError) as e:
+        g.adjoint(4)
+    assert e.value.code == lb.LB_EINVAL
+
+
 def test_fp32_shifted_state_roundtrip():
     w = I.emulsion_small()
     g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, precision=lb.LB_FP32_SHIFTED)
@@ -171,7 +227,11 @@ def test_full_size_1024x512_against_oracle(precision, steps, tol):
     against the oracle on every node (the OpenMP oracle finishes this in seconds)."""
     w = I.emulsion_1024x512()
     g, o = _pair(w.params, w.rho1, w.rho2, w.T0, precision=precision, omp=True)
-    g.autotune(launches=3)  # the benchmark times the autotuned tile
+    import torch
+
+    scratch = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    g.autotune(launches=3, scratch=scratch)  # the benchmark times the tile picked with L2 flushed
+    del scratch
     g.step(steps)
     o.step(steps)
     fg, fo = g.fields(), o.fields()
@@ -223,7 +283,7 @@ def test_init_errors():
     assert e.value.code == lb.LB_EINVAL
 
 
-@pytest.mark.parametrize("precision", [lb.LB_FP64, lb.LB_FP32_SHIFTED])
+@pytest.mark.parametrize("precision", [lb.LB_FP64, lb.LB_FP32_SHIFTED, lb.LB_FP32_FP16T])
 @pytest.mark.parametrize("periodic", [0, 1])
 @pytest.mark.parametrize("nx,ny", [(300, 130), (277, 45)])
 def test_every_tile_candidate_gives_identical_results(precision, periodic, nx, ny):
@@ -245,7 +305,7 @@ def test_every_tile_candidate_gives_identical_results(precision, periodic, nx, n
         mask = I.posts_mask(nx, ny, 4, 5, 25)
     ref = None
     n_cand = None
-    for k in range(16):
+    for k in range(64):
         g = lb.Lattice(params, r1, 1.5 - r1, T0, mask=mask, precision=precision)
         n_cand = g.tile_info(0)["candidates"]
         if k >= n_cand:
@@ -274,6 +334,25 @@ def test_autotune_keeps_state_and_picks_a_candidate():
     h = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, precision=lb.LB_FP32_SHIFTED)
     h.step(8)
     np.testing.assert_array_equal(g.get_state(), h.get_state())
+
+
+def test_cold_autotune_keeps_state_and_needs_scratch():
+    import ctypes
+
+    import torch
+
+    w = I.emulsion_small()
+    g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, precision=lb.LB_FP32_SHIFTED)
+    g.step(4)
+    before = g.get_state()
+    scratch = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    k, ms = g.autotune(launches=2, scratch=scratch)
+    assert 0 <= k < len(ms) and ms[k] == min(ms) and all(m > 0 for m in ms)
+    np.testing.assert_array_equal(g.get_state(), before)
+    assert g.tile_info()["tx"] == g.tile_info(k)["tx"]
+    chosen = ctypes.c_int()
+    rc = lb.lib().lb_autotune_cold(g._h, 2, None, 0, ctypes.byref(chosen), None, 0)
+    assert rc == lb.LB_EINVAL
 
 
 def test_fresh_handle_reports_no_error_on_reused_memory():
