@@ -12,9 +12,14 @@ fits in the 135 MB L2; the read leaves L2 holding clean lines, so the timed
 step does not pay for writing back the flush's own data).
 MLUPS = nx * ny * K / sum(step times) / 1e6 (all lattice nodes).
 
-Other forms on the same line: the batched 64-replica ensemble (aggregate
-MLUPS), and the adjoint on the 512 x 256 emulsion (time of one reverse step
-and of the whole sqrt(N)-checkpointed gradient against forward steps).
+Other forms on the same line: the FP32-fluid + FP16-thermal storage form on
+the same lattice (180 B per update); the batched 64-replica ensemble
+(aggregate MLUPS); the adjoint on the 512 x 256 emulsion (time of one reverse
+step and of the whole sqrt(N)-checkpointed gradient against forward steps);
+the 4096 x 2048 rough channel (8.4 M nodes, larger than L2); and the droplet
+topology analysis (labels, centres, digital Voronoi, Delaunay links) in
+milliseconds and in step equivalents.  Every step form picks its tile with
+the cold-L2 autotuner before timing.
 
 ``--impl reference`` times the FP64 CPU oracle (OpenMP build, all host
 cores) on the same workload and metric, each step a full lattice update.
@@ -51,10 +56,15 @@ def _peaks():
         return PEAKS_FALLBACK["hbm_gbs"], "fallback"
 
 
+# sources that define the step kernels (their DRAM counters go stale when one of these changes)
+STEP_KERNEL_SOURCES = ("lb_cfg.h", "lb_kernels.cuh", "lb_f32.cu", "lb_f64.cu", "lb_f32h.cu", "lb_tma_util.cuh",
+                       "lb_tma.cu", "lb_stream.cu")
+
+
 def _kernel_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2109_12565_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in STEP_KERNEL_SOURCES:
         with open(os.path.join(csrc, fn), "rb") as fh:
             h.update(fn.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -71,6 +81,14 @@ def _profile_counters():
     if d.get("kernel_sources_sha256_16") != _kernel_hash():
         return {}
     return d
+
+
+def _traffic(prof, form, tile):
+    """DRAM bytes per launch of the step kernel of this form and tile candidate, if captured."""
+    v = prof.get(f"{form}_step_dram_bytes_by_tile", {}).get(str(tile))
+    if v is None and prof.get(f"{form}_step_tile_candidate") == tile:
+        v = prof.get(f"{form}_step_dram_bytes_per_launch")
+    return v
 
 
 class ClockSampler:
@@ -330,6 +348,30 @@ def run_reference(args):
     return 0
 
 
+def time_droplets(w, I, lb, reps=5):
+    """Wall time of one droplet analysis (lb_droplets: labels, centres, digital Voronoi, links; a
+    synchronous call) on the 1024 x 512 emulsion and the 4096 x 2048 rough channel, median of reps
+    after one warm-up call."""
+    import torch
+
+    out = {}
+    for name, ww, prec in (("emulsion_1024x512", w, lb.LB_FP32_SHIFTED),
+                           ("rough_channel_4096x2048", I.rough_channel_4096x2048(), lb.LB_FP32_SHIFTED)):
+        g = lb.Lattice(ww.params, ww.rho1, ww.rho2, ww.T0, mask=ww.mask, precision=prec)
+        g.step(20)
+        res = g.droplets(0.8, arrays=False)
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = g.droplets(0.8, arrays=False)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        out[name] = {"ms": statistics.median(ts), "n_drops": res["n"], "n_links": res["n_links"]}
+        g.close()
+        del res
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -339,8 +381,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="fp32,fp64,batched,adjoint",
-                    help="comma list of fp32, fp64, batched, adjoint")
+    ap.add_argument("--forms", default="fp32,fp64,fp16t,batched,adjoint,rough,droplets",
+                    help="comma list of fp32, fp64, fp16t, batched, adjoint, rough, droplets")
+    ap.add_argument("--rough-steps", type=int, default=200, help="timed steps of the 4096 x 2048 rough channel")
     ap.add_argument("--fp64-steps", type=int, default=0, help="timed FP64 steps (default steps // 4)")
     ap.add_argument("--tile", type=int, default=-1, help="fixed tile candidate instead of autotuning")
     ap.add_argument("--batch-steps", type=int, default=200, help="timed steps of the 64-replica ensemble")
@@ -383,7 +426,11 @@ def main():
             r32 = time_form(w, lb.LB_FP32_SHIFTED, args.steps, args.warmup, flush, args.tile)
         if "fp64" in forms_req:
             r64 = time_form(w, lb.LB_FP64, steps64, args.warmup, flush, args.tile)
+        r16 = time_form(w, lb.LB_FP32_FP16T, args.steps, args.warmup, flush, -1) if "fp16t" in forms_req else None
         rb = time_batch(ens, args.batch_steps, args.warmup) if ens else None
+        wr = I.rough_channel_4096x2048() if "rough" in forms_req else None
+        rr = time_form(wr, lb.LB_FP32_SHIFTED, args.rough_steps, args.warmup, flush, -1) if wr else None
+    rdrop = time_droplets(w, I, lb) if "droplets" in forms_req else None
     radj = None
     if "adjoint" in forms_req:
         wa = I.emulsion_512x256()
@@ -416,7 +463,7 @@ def main():
     if r32:
         ach32 = bytes32 / (r32["ms_per_step"] * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s", "frac": ach32 / peak,
-                "traffic": prof.get("fp32_step_dram_bytes_per_launch"), "peak_source": peak_kind,
+                "traffic": _traffic(prof, "fp32", r32["tile"]["candidate"]), "peak_source": peak_kind,
                 "kernel": "lb_step_kernel<float, shifted> (fused step)", "algorithmic_bytes_per_launch": bytes32}
         forms["fp32_shifted"] = {"MLUPS": mlups32, "ms_per_step": r32["ms_per_step"], "hbm_frac": ach32 / peak,
                                  "GBps": ach32, "Nu": r32["obs"]["Nu"], "tile": r32["tile"]}
@@ -424,7 +471,7 @@ def main():
         ach64 = bytes64 / (r64["ms_per_step"] * 1e-3) / 1e9
         forms["fp64"] = {"MLUPS": mlups64, "ms_per_step": r64["ms_per_step"], "hbm_frac": ach64 / peak,
                          "GBps": ach64, "bound": "alu (FP64 pipe)",
-                         "traffic": prof.get("fp64_step_dram_bytes_per_launch"), "Nu": r64["obs"]["Nu"],
+                         "traffic": _traffic(prof, "fp64", r64["tile"]["candidate"]), "Nu": r64["obs"]["Nu"],
                          "tile": r64["tile"]}
         dp = prof.get("fp64_dp_flops_per_node")
         if dp:
@@ -432,6 +479,24 @@ def main():
             forms["fp64"]["alu_frac_of_nominal"] = forms["fp64"]["dp_tflops"] / FP64_NOMINAL_TFLOPS
     if r32 and r64:
         forms["fp32_over_fp64"] = mlups32 / mlups64
+    if r16:
+        ach16 = 180.0 * N / (r16["ms_per_step"] * 1e-3) / 1e9  # 18 FP32 + 9 FP16 values read + written
+        forms["fp32_fp16_thermal"] = {"MLUPS": N / (r16["ms_per_step"] * 1e3), "ms_per_step": r16["ms_per_step"],
+                                      "hbm_frac": ach16 / peak, "GBps": ach16, "bytes_per_update": 180,
+                                      "traffic": _traffic(prof, "fp16t", r16["tile"]["candidate"]),
+                                      "Nu": r16["obs"]["Nu"], "tile": r16["tile"]}
+    if rr:
+        Nr = wr.params["nx"] * wr.params["ny"]
+        achr = 216.0 * Nr / (rr["ms_per_step"] * 1e-3) / 1e9
+        forms["rough_channel_4096x2048"] = {"MLUPS": Nr / (rr["ms_per_step"] * 1e3), "ms_per_step": rr["ms_per_step"],
+                                            "hbm_frac": achr / peak, "GBps": achr, "steps": args.rough_steps,
+                                            "precision": "fp32_shifted", "Nu": rr["obs"]["Nu"], "tile": rr["tile"]}
+    if rdrop:
+        step_ms = r32["ms_per_step"] if r32 else None
+        for k, v in rdrop.items():
+            if k == "emulsion_1024x512" and step_ms:
+                v["fp32_step_equivalents"] = v["ms"] / step_ms
+        forms["droplets"] = rdrop
     if radj:
         forms["adjoint"] = dict(workload="emulsion_512x256", **{k: v for k, v in radj.items()})
     if rb:
@@ -461,7 +526,8 @@ def main():
         "roofline": roof,
         "forms": forms,
         "e2e": e2e,
-        "gpu_launches": (args.steps if r32 else 0) + (steps64 if r64 else 0) + (
+        "gpu_launches": (args.steps if r32 else 0) + (steps64 if r64 else 0) + (args.steps if r16 else 0) + (
+            args.rough_steps if rr else 0) + (
             (args.batch_steps if rb["info"]["schedule"] == 0 else -(-args.batch_steps // 64)) if rb else 0),
         "clocks": clk.summary(),
     }

@@ -142,10 +142,11 @@ int lb_set_state(lb_handle* h, const double* host, size_t bytes);
 int lb_autotune(lb_handle* h, int launches, int* chosen, double* ms_per_candidate, int n_slots);
 
 /* The same autotuner for runs whose state does not stay in L2 between steps (not in the paper).
- * Before each timed launch it writes scratch_bytes of the caller's device buffer d_scratch (give
- * more than the L2 size; it is overwritten, not read), so every trial starts with the populations
- * evicted from L2; only the launches are timed.  Returns LB_EINVAL without a scratch buffer.  The
- * state and the step counter do not change.  Synchronous. */
+ * Before each timed launch it writes the first half of the caller's device buffer d_scratch and reads
+ * the second half (give at least twice the L2 size, 16-byte aligned; its contents are overwritten),
+ * so every trial starts with the populations evicted and L2 holding clean lines; only the launches
+ * are timed.  Returns LB_EINVAL without a scratch buffer.  The state and the step counter do not
+ * change.  Synchronous. */
 int lb_autotune_cold(lb_handle* h, int launches, void* d_scratch, size_t scratch_bytes, int* chosen,
                      double* ms_per_candidate, int n_slots);
 
@@ -312,6 +313,14 @@ int lb_droplets(lb_handle* h, double threshold, int max_drops, void* d_ws, size_
  * ints, x fastest: droplet id / -1, Voronoi colour / -1).  Synchronous. */
 int lb_droplets_get(lb_handle* h, const void* d_ws, size_t ws_bytes, double* cx, double* cy, long long* size,
                     int* links, int* label, int* color);
+
+/* Droplet Nusselt number (Eq. NuDrops) of every droplet of an analysis of the CURRENT state (run
+ * lb_droplets first, without stepping in between): (u_y T - kappa dT/dy) / (kappa Delta T / H) at the
+ * node nearest to the centre (x rounded half up, periodic; y rounded half up), u_y = u^(H)_y, dT/dy
+ * central with the mirror 2 T_w - T at a solid neighbour, kappa = (tau_g - 1/2) / 3, H = ny - 2.  nu:
+ * host array of n_drops doubles; 0 when periodic_y or T_down = T_up, NaN when the nearest node is
+ * solid.  Synchronous. */
+int lb_droplets_nusselt(lb_handle* h, const void* d_ws, size_t ws_bytes, double* nu);
 
 /* Plastic (T1) events between two analyses of this lattice (Sec. 2.4, diagonal flip of a
  * quadrilateral): a droplet of the later analysis matches one of the earlier when each is the

@@ -310,3 +310,46 @@ def t1_compare(params, prev, now, d_max):
     t1 = sorted((a, b, c, d) for a, b in broken for c, d in arising
                 if linked(a, c) and linked(a, d) and linked(b, c) and linked(b, d))
     return {"matched": len(n2p), "broken": broken, "arising": arising, "t1": t1}
+
+
+def droplet_nusselt(params, fields, cx, cy, mask=None):
+    """Droplet Nusselt number of Eq. NuDrops for every droplet centre (cx[i], cy[i]).
+
+    u_y = u^(H)_y, T and dT/dy are taken at the lattice node nearest to the centre (x rounded half
+    up, periodic; y rounded half up): dT/dy = (T(y+1) - T(y-1)) / 2 with the mirror 2 T_w - T(y) at a
+    solid neighbour (the same rule as Eq. NuTime), kappa = (tau_g - 1/2) / 3, "ny" of the formula the
+    wall-to-wall height H = ny - 2, Delta T = T_down - T_up.  0 when periodic in y or Delta T = 0; NaN
+    when the nearest node is solid."""
+    nx, ny = int(params["nx"]), int(params["ny"])
+    per_y = bool(params.get("periodic_y", 0))
+    Td, Tu = float(params["T_down"]), float(params["T_up"])
+    dT = Td - Tu
+    kappa = (float(params["tau_g"]) - 0.5) / 3.0
+    H = float(ny - 2)
+    solid = np.zeros((ny, nx), dtype=bool)
+    if not per_y:
+        solid[0, :] = solid[-1, :] = True
+    if mask is not None:
+        solid |= np.asarray(mask) != 0
+    T, uy = fields["T"], fields["uy"]
+    out = np.zeros(len(cx))
+    if per_y or dT == 0.0:
+        return out
+    den = kappa * (dT / H)
+    for i in range(len(cx)):
+        x = int(np.floor(cx[i] + 0.5)) % nx
+        y = min(max(int(np.floor(cy[i] + 0.5)), 0), ny - 1)
+        if solid[y, x]:
+            out[i] = np.nan
+            continue
+        t = T[y, x]
+
+        def neighbour(yy):
+            if solid[yy, x]:
+                tw = Td if 2 * yy < ny else Tu
+                return 2.0 * tw - t
+            return T[yy, x]
+
+        dTdy = 0.5 * (neighbour(y + 1) - neighbour(y - 1))
+        out[i] = (uy[y, x] * t - kappa * dTdy) / den
+    return out

@@ -324,19 +324,42 @@ __device__ __forceinline__ long long min_image_i(long long d, int n) {
   return d;
 }
 
+// Sums of a lane group (lanes with equal key within the warp): every lane of the group gets the total.
+__device__ __forceinline__ long long group_sum(unsigned group, long long v) {
+  long long total = 0;
+  unsigned m = group;
+  while (m) {  // at most 32 iterations: one per member
+    const int src = __ffs(m) - 1;
+    total += __shfl_sync(group, v, src);
+    m &= m - 1;
+  }
+  return total;
+}
+
 __global__ void centre_sums(Geo g, const int* __restrict__ did, const int* __restrict__ root, int n_drops,
                             unsigned long long* cnt, long long* sx, long long* sy) {
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= (long long)g.nx * g.ny) return;
-  const int d = did[n];
-  if (d < 0 || d >= n_drops) return;
-  const int r = root[d];
-  const long long x = n % g.nx, y = n / g.nx, rx = r % g.nx, ry = r / g.nx;
-  const long long dx = min_image_i(x - rx, g.nx);
-  const long long dy = g.periodic_y ? min_image_i(y - ry, g.ny) : (y - ry);
-  atomicAdd(cnt + d, 1ull);
-  atomicAdd(reinterpret_cast<unsigned long long*>(sx + d), (unsigned long long)dx);
-  atomicAdd(reinterpret_cast<unsigned long long*>(sy + d), (unsigned long long)dy);
+  const bool in = n < (long long)g.nx * g.ny;
+  const int d = in ? did[n] : -1;
+  const bool mine = d >= 0 && d < n_drops;
+  long long dx = 0, dy = 0;
+  if (mine) {
+    const int r = root[d];
+    const long long x = n % g.nx, y = n / g.nx, rx = r % g.nx, ry = r / g.nx;
+    dx = min_image_i(x - rx, g.nx);
+    dy = g.periodic_y ? min_image_i(y - ry, g.ny) : (y - ry);
+  }
+  // lanes of one warp mostly see the same droplet: one atomic per (warp, droplet) group, integer sums
+  const unsigned active = __ballot_sync(0xffffffffu, mine);
+  if (!mine) return;
+  const unsigned group = __match_any_sync(active, d);
+  const long long gx = group_sum(group, dx), gy = group_sum(group, dy);
+  const int lane = threadIdx.x & 31;
+  if (lane == __ffs(group) - 1) {
+    atomicAdd(cnt + d, (unsigned long long)__popc(group));
+    atomicAdd(reinterpret_cast<unsigned long long*>(sx + d), (unsigned long long)gx);
+    atomicAdd(reinterpret_cast<unsigned long long*>(sy + d), (unsigned long long)gy);
+  }
 }
 
 __global__ void centre_final(Geo g, int n_drops, const int* __restrict__ root, const unsigned long long* __restrict__ cnt,
@@ -602,7 +625,7 @@ __global__ void link_changes(int mode, int n, const int* __restrict__ adj_self, 
 __global__ void t1_events(int n_broken, const int* __restrict__ broken, const int* __restrict__ adj_p,
                           const int* __restrict__ deg_p, const int* __restrict__ adj_n, const int* __restrict__ deg_n,
                           const int* __restrict__ p2n, const int* __restrict__ cnt_off, int* __restrict__ counts,
-                          int* __restrict__ out) {
+                          int* __restrict__ out, long long out_cap) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_broken) return;
   const int a = broken[2 * k], b = broken[2 * k + 1];
@@ -617,7 +640,7 @@ __global__ void t1_events(int n_broken, const int* __restrict__ broken, const in
       if (!has_link(adj_p, deg_p, b, d) || has_link(adj_p, deg_p, c, d)) continue;
       const int nc = p2n[c], nd = p2n[d];
       if (nc < 0 || nd < 0 || !has_link(adj_n, deg_n, nc, nd)) continue;
-      if (out) {
+      if (out && o + cnt < out_cap) {  // out holds out_cap quadruples
         out[4 * (o + cnt)] = a;
         out[4 * (o + cnt) + 1] = b;
         out[4 * (o + cnt) + 2] = c < d ? c : d;
@@ -627,6 +650,39 @@ __global__ void t1_events(int n_broken, const int* __restrict__ broken, const in
     }
   }
   if (!out) counts[k] = cnt;
+}
+
+// Droplet Nusselt number (Eq. NuDrops) at the node nearest to each centre (x rounded half up,
+// periodic; y rounded half up and clamped): (u_y T - kappa dT/dy) / (kappa Delta T / H), dT/dy central
+// with the mirror 2 T_w - T at a solid neighbour.  Unfused double arithmetic in the oracle's order.
+// NaN when the nearest node is solid.  fields: 5 planes rho1, rho2, T, ux, uy of nx * ny doubles.
+__global__ void droplet_nusselt(Geo g, int n_drops, const double* __restrict__ cx, const double* __restrict__ cy,
+                                const double* __restrict__ fields, double kappa, double den, double T_down,
+                                double T_up, double* __restrict__ nu) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_drops) return;
+  const long long N = (long long)g.nx * g.ny;
+  int x = (int)floor(__dadd_rn(cx[i], 0.5)) % g.nx;
+  int y = (int)floor(__dadd_rn(cy[i], 0.5));
+  y = y < 0 ? 0 : (y > g.ny - 1 ? g.ny - 1 : y);
+  if (is_solid(g, x, y)) {
+    nu[i] = __longlong_as_double(0x7ff8000000000000ll);  // quiet NaN
+    return;
+  }
+  const double* T = fields + 2 * N;
+  const double* uy = fields + 4 * N;
+  const long long n = (long long)y * g.nx + x;
+  const double t = T[n];
+  auto neighbour = [&](int yy) {
+    if (g.periodic_y) yy = (yy + g.ny) % g.ny;
+    if (is_solid(g, x, yy)) {
+      const double tw = (2 * yy < g.ny) ? T_down : T_up;
+      return __dsub_rn(__dmul_rn(2.0, tw), t);
+    }
+    return T[(long long)yy * g.nx + x];
+  };
+  const double dTdy = __dmul_rn(0.5, __dsub_rn(neighbour(y + 1), neighbour(y - 1)));
+  nu[i] = __ddiv_rn(__dsub_rn(__dmul_rn(uy[n], t), __dmul_rn(kappa, dTdy)), den);
 }
 
 inline unsigned nb(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -794,6 +850,37 @@ int lb_droplets_get(lb_handle* h, const void* d_ws, size_t ws_bytes, double* cx,
   return LB_OK;
 }
 
+int lb_droplets_nusselt(lb_handle* h, const void* d_ws, size_t ws_bytes, double* nu) {
+  if (!h || !d_ws || !nu) return LB_EINVAL;
+  Header hd{};
+  if (int rc = read_header(h, d_ws, &hd)) return rc;
+  DLayout L;
+  if (hd.max_drops < 1 || hd.nx != h->p.nx || hd.ny != h->p.ny || !check_ws(h, d_ws, ws_bytes, hd.max_drops, &L))
+    return dfail(h, LB_EINVAL, "workspace does not hold a droplet analysis of this lattice");
+  const int M = hd.n_drops;
+  if (M == 0) return LB_OK;
+  const double dT = h->p.T_down - h->p.T_up;
+  if (h->p.periodic_y || dT == 0.0) {
+    for (int i = 0; i < M; ++i) nu[i] = 0.0;
+    return LB_OK;
+  }
+  const DView v = view(const_cast<void*>(d_ws), L);
+  const Geo g{h->p.nx, h->p.ny, h->p.periodic_y, h->cfg.mask};
+  double* stage = static_cast<double*>(h->buf[h->cur ^ 1]);
+  double* dnu = stage + 5 * L.N;  // the staging buffer holds at least 9 doubles per node
+  const double kappa = (h->p.tau_g - 0.5) / 3.0;
+  const double den = kappa * (dT / (double)(h->p.ny - 2));
+  cudaError_t e = fields_into(h, stage);
+  if (e == cudaSuccess) {
+    droplet_nusselt<<<nb(M, 256), 256, 0, h->stream>>>(g, M, v.cx, v.cy, stage, kappa, den, h->p.T_down, h->p.T_up, dnu);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(nu, dnu, (size_t)M * 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets_nusselt", e);
+  return LB_OK;
+}
+
 int lb_droplets_compare(lb_handle* h, const void* d_ws_prev, const void* d_ws_now, size_t ws_bytes, double d_max,
                         void* d_scratch, size_t scratch_bytes, int* counts4, int* broken, int* arising, int* t1,
                         int cap) {
@@ -871,10 +958,12 @@ int lb_droplets_compare(lb_handle* h, const void* d_ws_prev, const void* d_ws_no
     if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets_compare", e);
   }
   if (tot[0] > 0) {
-    t1_events<<<nb(tot[0], T), T, 0, s>>>(tot[0], dbroken, vp.adj, vp.deg, vn.adj, vn.deg, p2n, nullptr, cnt[2], nullptr);
+    t1_events<<<nb(tot[0], T), T, 0, s>>>(tot[0], dbroken, vp.adj, vp.deg, vn.adj, vn.deg, p2n, nullptr, cnt[2], nullptr,
+                                          0);
     e = exclusive_scan(cnt[2], tot[0], off[2], blk[2], s);
     if (e == cudaSuccess) {
-      t1_events<<<nb(tot[0], T), T, 0, s>>>(tot[0], dbroken, vp.adj, vp.deg, vn.adj, vn.deg, p2n, off[2], nullptr, dt1);
+      t1_events<<<nb(tot[0], T), T, 0, s>>>(tot[0], dbroken, vp.adj, vp.deg, vn.adj, vn.deg, p2n, off[2], nullptr, dt1,
+                                            (long long)lmax);
       e = cudaMemcpyAsync(&tot[2], blk[2] + nb(tot[0], kScanBlock), sizeof(int), cudaMemcpyDeviceToHost, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -896,7 +985,9 @@ int lb_droplets_compare(lb_handle* h, const void* d_ws_prev, const void* d_ws_no
   if (broken && tot[0]) e = cudaMemcpyAsync(broken, dbroken, (size_t)(tot[0] < cap ? tot[0] : cap) * 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && arising && tot[1])
     e = cudaMemcpyAsync(arising, darising, (size_t)(tot[1] < cap ? tot[1] : cap) * 8, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && t1 && tot[2]) e = cudaMemcpyAsync(t1, dt1, (size_t)(tot[2] < cap ? tot[2] : cap) * 16, cudaMemcpyDeviceToHost, s);
+  const int t1_held = tot[2] < (int)lmax ? tot[2] : (int)lmax;  // the device list keeps the first lmax events
+  if (e == cudaSuccess && t1 && t1_held)
+    e = cudaMemcpyAsync(t1, dt1, (size_t)(t1_held < cap ? t1_held : cap) * 16, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets_compare", e);
   return LB_OK;

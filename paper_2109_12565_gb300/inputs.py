@@ -194,9 +194,10 @@ def emulsion_512x256(seed=4):
 
 def rough_channel_4096x2048(seed=5):
     """Large rough channel: 4096 x 2048, posts 8 x 8 every 32 columns on both walls, ~5000 droplets
-    (100 x 50) at phi = 0.8 of the slab between the post tops."""
+    (94 x 53 = 4982 on a near-isotropic honeycomb: x spacing 43.6, row spacing 38.3) at phi = 0.8 of
+    the slab between the post tops, so d = 41.2 and neighbouring disks start ~2.4 nodes apart."""
     mask = posts_mask(4096, 2048, 8, 8, 32)
-    w = emulsion_hex(4096, 2048, 100, 50, 0.8, 3.6e4, seed, mask=mask, post_h=8, name="rough_channel_4096x2048")
+    w = emulsion_hex(4096, 2048, 94, 53, 0.8, 3.6e4, seed, mask=mask, post_h=8, name="rough_channel_4096x2048")
     w.nsteps = 50000
     return w
 

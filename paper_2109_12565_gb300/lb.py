@@ -25,7 +25,8 @@ EXPORTS = ("lb_workspace_size", "lb_init", "lb_step", "lb_observables", "lb_get_
            "lb_batch_autotune", "lb_batch_info", "lb_batch_observables", "lb_batch_get_fields", "lb_batch_get_state",
            "lb_batch_sync", "lb_batch_set_wait_budget", "lb_batch_destroy", "lb_batch_last_error",
            "lb_state_layout", "lb_adjoint_workspace_size", "lb_adjoint_step", "lb_adjoint", "lb_adjoint_timing",
-           "lb_droplets_workspace_size", "lb_droplets", "lb_droplets_get", "lb_droplets_compare")
+           "lb_droplets_workspace_size", "lb_droplets", "lb_droplets_get", "lb_droplets_nusselt",
+           "lb_droplets_compare")
 
 
 class LbError(RuntimeError):
@@ -114,7 +115,9 @@ def lib():
                                       ctypes.POINTER(i), ctypes.POINTER(i)]
         L.lb_droplets_compare.argtypes = [vp, vp, vp, sz, ctypes.c_double, vp, sz, ctypes.POINTER(i),
                                           ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), i]
-        for f in ("lb_droplets_workspace_size", "lb_droplets", "lb_droplets_get", "lb_droplets_compare"):
+        L.lb_droplets_nusselt.argtypes = [vp, vp, sz, dp]
+        for f in ("lb_droplets_workspace_size", "lb_droplets", "lb_droplets_get", "lb_droplets_nusselt",
+                  "lb_droplets_compare"):
             getattr(L, f).restype = ctypes.c_int
         L.lb_version.argtypes = []
         L.lb_version.restype = ctypes.c_char_p
@@ -282,6 +285,13 @@ class Lattice:
             out.update(cx=cx[:M.value], cy=cy[:M.value], size=size[:M.value], links=links[:K.value], label=label,
                        color=color)
         return out
+
+    def droplet_nusselt(self, res):
+        """Eq. NuDrops for every droplet of a droplets() result taken on the current state."""
+        nu = np.zeros(max(res["n"], 1))
+        _check(lib().lb_droplets_nusselt(self._h, ctypes.c_void_p(res["ws"].data_ptr()), res["ws_bytes"], _dp(nu)),
+               self._h)
+        return nu[:res["n"]]
 
     def droplet_t1(self, prev, now, d_max, cap=None):
         """T1 events between two results of droplets() (lb_droplets_compare)."""

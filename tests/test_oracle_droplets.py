@@ -181,3 +181,25 @@ def test_t1_flip_of_a_quadrilateral_diagonal():
     # nothing happens when the frame is compared with itself
     same = O.t1_compare(p, prev, prev, d_max=8.0)
     assert same["broken"] == same["arising"] == same["t1"] == []
+
+
+def test_droplet_nusselt_closed_forms():
+    """Eq. NuDrops: in pure conduction (u = 0, T linear between the half-way walls) every droplet has
+    Nu = 1, also next to the walls where the mirror rule enters; a uniform u_y U at uniform T0 gives
+    U T0 / (kappa Delta T / H)."""
+    nx, ny = 80, 40
+    p = dict(_params(nx, ny), T_down=1.0, T_up=0.0, tau_g=0.8)
+    H = ny - 2
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    T_lin = 1.0 - (y - 0.5) / H
+    fields = {"T": T_lin, "uy": np.zeros((ny, nx))}
+    cx = np.array([3.2, 40.0, 79.6, 10.0, 20.0])
+    cy = np.array([1.2, 20.4, 38.3, 37.9, 0.6])
+    nu = O.droplet_nusselt(p, fields, cx, cy)
+    np.testing.assert_allclose(nu, 1.0, rtol=0, atol=1e-12)
+    kappa = (0.8 - 0.5) / 3.0
+    fields = {"T": np.full((ny, nx), 0.3), "uy": np.full((ny, nx), 2e-3)}
+    nu = O.droplet_nusselt(p, fields, np.array([40.0]), np.array([20.0]))
+    assert abs(nu[0] - 2e-3 * 0.3 / (kappa * 1.0 / H)) < 1e-12
+    # periodic y or no temperature difference: 0 by convention
+    assert O.droplet_nusselt(dict(p, periodic_y=1), fields, cx, cy).tolist() == [0.0] * 5
