@@ -83,6 +83,24 @@ def _profile_counters():
     return d
 
 
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of a list of floats over all ranks (one all-reduce), or the list itself
+    without a process group.  Every rank must call it, before any rank leaves."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def aggregate_mlups(world, nodes, steps, t_ms_max):
+    """Whole-job MLUPS: every rank updates `nodes` nodes `steps` times; the job takes the slowest
+    rank's time (milliseconds)."""
+    return world * nodes * steps / (t_ms_max * 1e3)
+
+
 def _traffic(prof, form, tile):
     """DRAM bytes per launch of the step kernel of this form and tile candidate, if captured."""
     v = prof.get(f"{form}_step_dram_bytes_by_tile", {}).get(str(tile))
@@ -385,7 +403,8 @@ def main():
                     help="comma list of fp32, fp64, fp16t, batched, adjoint, rough, droplets")
     ap.add_argument("--rough-steps", type=int, default=200, help="timed steps of the 4096 x 2048 rough channel")
     ap.add_argument("--fp64-steps", type=int, default=0, help="timed FP64 steps (default steps // 4)")
-    ap.add_argument("--tile", type=int, default=-1, help="fixed tile candidate instead of autotuning")
+    ap.add_argument("--tile", type=int, default=-1,
+                    help="fixed tile candidate (index within the precision's own list) instead of autotuning")
     ap.add_argument("--batch-steps", type=int, default=200, help="timed steps of the 64-replica ensemble")
     ap.add_argument("--adjoint-steps", type=int, default=2000, help="N of the adjoint gradient (512 x 256)")
     args = ap.parse_args()
@@ -426,10 +445,10 @@ def main():
             r32 = time_form(w, lb.LB_FP32_SHIFTED, args.steps, args.warmup, flush, args.tile)
         if "fp64" in forms_req:
             r64 = time_form(w, lb.LB_FP64, steps64, args.warmup, flush, args.tile)
-        r16 = time_form(w, lb.LB_FP32_FP16T, args.steps, args.warmup, flush, -1) if "fp16t" in forms_req else None
+        r16 = time_form(w, lb.LB_FP32_FP16T, args.steps, args.warmup, flush, args.tile) if "fp16t" in forms_req else None
         rb = time_batch(ens, args.batch_steps, args.warmup) if ens else None
         wr = I.rough_channel_4096x2048() if "rough" in forms_req else None
-        rr = time_form(wr, lb.LB_FP32_SHIFTED, args.rough_steps, args.warmup, flush, -1) if wr else None
+        rr = time_form(wr, lb.LB_FP32_SHIFTED, args.rough_steps, args.warmup, flush, args.tile) if wr else None
     rdrop = time_droplets(w, I, lb) if "droplets" in forms_req else None
     radj = None
     if "adjoint" in forms_req:
@@ -437,21 +456,16 @@ def main():
         radj = {"fp64": time_adjoint(wa, lb.LB_FP64, args.adjoint_steps),
                 "fp32_shifted": time_adjoint(wa, lb.LB_FP32_SHIFTED, args.adjoint_steps)}
     torch.cuda.synchronize()
-    t32 = r32["ms_total"] if r32 else 0.0
-    t64 = r64["ms_total"] if r64 else 0.0
-    if dist:
-        t = torch.tensor([t32, t64], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t32, t64 = float(t[0]), float(t[1])
-    mlups32 = world * N * args.steps / (t32 * 1e3) if r32 else None
-    mlups64 = world * N * steps64 / (t64 * 1e3) if r64 else None
-    e2e = None
-    if args.e2e_steps > 0:
-        e2e = time_e2e(w, lb.LB_FP32_SHIFTED, args.e2e_steps)
-        if dist:
-            t = torch.tensor([e2e["seconds"]], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e["value"] = world * N * args.e2e_steps / float(t[0]) / 1e6
+    e2e = time_e2e(w, lb.LB_FP32_SHIFTED, args.e2e_steps) if args.e2e_steps > 0 else None
+    # every rank's timed totals, max over ranks, before rank 0 alone goes on to report
+    t32, t64, t16, trr, tb, te2e = max_over_ranks(
+        [r32["ms_total"] if r32 else 0.0, r64["ms_total"] if r64 else 0.0, r16["ms_total"] if r16 else 0.0,
+         rr["ms_total"] if rr else 0.0, rb["ms_total"] if rb else 0.0, e2e["seconds"] if e2e else 0.0],
+        dist, "cuda")
+    mlups32 = aggregate_mlups(world, N, args.steps, t32) if r32 else None
+    mlups64 = aggregate_mlups(world, N, steps64, t64) if r64 else None
+    if e2e:
+        e2e["value"] = aggregate_mlups(world, N, args.e2e_steps, te2e * 1e3)
     if rank != 0:
         dist.destroy_process_group()
         return 0
@@ -481,14 +495,16 @@ def main():
         forms["fp32_over_fp64"] = mlups32 / mlups64
     if r16:
         ach16 = 180.0 * N / (r16["ms_per_step"] * 1e-3) / 1e9  # 18 FP32 + 9 FP16 values read + written
-        forms["fp32_fp16_thermal"] = {"MLUPS": N / (r16["ms_per_step"] * 1e3), "ms_per_step": r16["ms_per_step"],
+        forms["fp32_fp16_thermal"] = {"MLUPS": aggregate_mlups(world, N, args.steps, t16),
+                                      "ms_per_step": r16["ms_per_step"],
                                       "hbm_frac": ach16 / peak, "GBps": ach16, "bytes_per_update": 180,
                                       "traffic": _traffic(prof, "fp16t", r16["tile"]["candidate"]),
                                       "Nu": r16["obs"]["Nu"], "tile": r16["tile"]}
     if rr:
         Nr = wr.params["nx"] * wr.params["ny"]
         achr = 216.0 * Nr / (rr["ms_per_step"] * 1e-3) / 1e9
-        forms["rough_channel_4096x2048"] = {"MLUPS": Nr / (rr["ms_per_step"] * 1e3), "ms_per_step": rr["ms_per_step"],
+        forms["rough_channel_4096x2048"] = {"MLUPS": aggregate_mlups(world, Nr, args.rough_steps, trr),
+                                            "ms_per_step": rr["ms_per_step"],
                                             "hbm_frac": achr / peak, "GBps": achr, "steps": args.rough_steps,
                                             "precision": "fp32_shifted", "Nu": rr["obs"]["Nu"], "tile": rr["tile"]}
     if rdrop:
@@ -500,13 +516,8 @@ def main():
     if radj:
         forms["adjoint"] = dict(workload="emulsion_512x256", **{k: v for k, v in radj.items()})
     if rb:
-        tb = rb["ms_total"]
-        if dist:
-            t = torch.tensor([tb], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tb = float(t[0])
         achb = 216.0 * rb["nodes"] / (rb["ms_per_step"] * 1e-3) / 1e9
-        forms["batched"] = {"MLUPS": world * rb["nodes"] * args.batch_steps / (tb * 1e3), "replicas": len(ens),
+        forms["batched"] = {"MLUPS": aggregate_mlups(world, rb["nodes"], args.batch_steps, tb), "replicas": len(ens),
                             "nodes": rb["nodes"], "ms_per_step": rb["ms_per_step"], "hbm_frac": achb / peak,
                             "GBps": achb, "schedule": ["per-step graph", "persistent"][rb["info"]["schedule"]],
                             "tile_candidate": rb["info"]["tile"], "work_items": rb["info"]["items"],

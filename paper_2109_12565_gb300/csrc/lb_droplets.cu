@@ -33,7 +33,7 @@ namespace drops {
 
 constexpr int kMaxDeg = 32;     // links per droplet held in the adjacency set
 constexpr int kScanBlock = 1024;
-constexpr int kCell = 16;       // target edge of a centre-grid cell (nodes)
+constexpr int kCell = 32;       // target edge of a centre-grid cell (nodes): about one droplet spacing
 constexpr int kErrDegree = 1;   // a droplet has more than kMaxDeg links
 constexpr int kErrDrops = 2;    // more droplets than max_drops
 constexpr int kErrUnion = 4;    // a union-find loop ran past its bound

@@ -23,6 +23,10 @@ const Cand kCands[] = {
     {{128, 16, 2, 3}, launch_step_shape<float, true, 128, 16, 2, 3>},
     {{64, 8, 4, 4}, launch_step_shape<float, true, 64, 8, 4, 4>},
     {{32, 32, 8, 3}, launch_step_shape<float, true, 32, 32, 8, 3>},
+    {{64, 16, 4, 4}, launch_step_shape<float, true, 64, 16, 4, 4>},
+    {{32, 16, 8, 4}, launch_step_shape<float, true, 32, 16, 8, 4>},
+    {{64, 32, 4, 4}, launch_step_shape<float, true, 64, 32, 4, 4>},
+    {{32, 32, 8, 4}, launch_step_shape<float, true, 32, 32, 8, 4>},
 };
 }  // namespace
 

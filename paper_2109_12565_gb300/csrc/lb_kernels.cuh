@@ -181,6 +181,129 @@ template <class C, int TX, int TY, bool NEED_T> struct TileSmem {
   unsigned char solid[RY][RX];
 };
 
+// Two-byte-aligned pair load of populations (8-byte vector load of two FP32 nodes).
+template <bool CG> __device__ __forceinline__ float2 ld_pop2(const float2* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+template <class C, int TX, int TY, bool NEED_T>
+__device__ __forceinline__ void phase_a_wall(TileSmem<C, TX, TY, NEED_T>& sm, const KParams<C>& kp, int rx, int ry) {
+  sm.rho[0][ry][rx] = kp.drho_w[0];
+  sm.rho[1][ry][rx] = kp.drho_w[1];
+  sm.psi[0][ry][rx] = kp.psi_w[0];
+  sm.psi[1][ry][rx] = kp.psi_w[1];
+  sm.solid[ry][rx] = 1;
+}
+
+// Sums of one component's 9 populations for phase A: density deviation and the two momentum parts,
+// in the order of phase_a_node.
+template <class C> struct CompSums {
+  C d, jx, jy;
+};
+template <class C> __device__ __forceinline__ CompSums<C> comp_sums(const C f[9]) {
+  CompSums<C> r;
+  r.d = C(0);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) r.d += f[i];
+  r.jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+  r.jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+  return r;
+}
+
+// The store part of phase_a_node from the component sums (same values, same rounding).
+template <class C, bool SHIFT, int TX, int TY, bool NEED_T>
+__device__ __forceinline__ void phase_a_store(TileSmem<C, TX, TY, NEED_T>& sm, const KParams<C>& kp, int rx, int ry,
+                                              const CompSums<C>& a, const CompSums<C>& b) {
+  const C rb0 = SHIFT ? kp.rho_bar[0] : C(0), rb1 = SHIFT ? kp.rho_bar[1] : C(0);
+  sm.rho[0][ry][rx] = a.d;
+  sm.rho[1][ry][rx] = b.d;
+  sm.psi[0][ry][rx] = psi_exp<C>(a.d + rb0, kp.rho0, kp.inv_rho0);
+  sm.psi[1][ry][rx] = psi_exp<C>(b.d + rb1, kp.rho0, kp.inv_rho0);
+  if (rx >= 2 && rx < TX + 2 && ry >= 2 && ry < TY + 2) {
+    sm.jx[ry - 2][rx - 2] = a.jx + b.jx;
+    sm.jy[ry - 2][rx - 2] = a.jy + b.jy;
+  }
+  sm.solid[ry][rx] = 0;
+}
+
+// Phase A of a step with FP32 fluid storage, two horizontally adjacent region nodes per thread: the
+// pair's populations come in as 8-byte loads when both nodes are fluid, contiguous and 8-byte
+// aligned (no periodic split between them), else node by node.  Component 1 is loaded and reduced
+// before component 2, which keeps 18 values live.  Per node the same arithmetic as the one-node loop,
+// so the results are bit-identical.
+template <class S, class C, bool SHIFT, int TX, int TY, int NT, bool CG>
+__device__ __forceinline__ int tile_phase_a_pairs(const SF<S>* __restrict__ fin, const KParams<C>& kp, int x0, int y0,
+                                                  TileSmem<C, TX, TY, false>& sm, int tid) {
+  constexpr int RX = TX + 4, RY = TY + 4, PX = RX / 2;
+  static_assert(RX % 2 == 0, "pairs need an even region width");
+  const int nx = kp.nx, ny = kp.ny, pitch = kp.pitch, plane = kp.plane;
+  const bool small_x = nx < TX + 4, small_y = ny < TY + 4;
+  int ring_solid = 0;
+  for (int r = tid; r < PX * RY; r += NT) {
+    const int ry = r / PX, rx = 2 * (r - ry * PX);
+    const int gxr = x0 + rx - 2;
+    int gxa, gxb;
+    if (small_x) {
+      gxa = wrap_any(gxr, nx);
+      gxb = wrap_any(gxr + 1, nx);
+    } else {
+      gxa = gxr < 0 ? gxr + nx : (gxr >= nx ? gxr - nx : gxr);
+      const int t = gxr + 1;
+      gxb = t < 0 ? t + nx : (t >= nx ? t - nx : t);
+    }
+    int gy = y0 + ry - 2;
+    bool sa, sb;
+    if (kp.periodic_y) {
+      gy = small_y ? wrap_any(gy, ny) : (gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy));
+      sa = kp.mask != nullptr && kp.mask[gy * nx + gxa] != 0;
+      sb = kp.mask != nullptr && kp.mask[gy * nx + gxb] != 0;
+    } else {
+      const bool wall = gy <= 0 || gy >= ny - 1;
+      sa = wall || (kp.mask != nullptr && kp.mask[gy * nx + gxa] != 0);
+      sb = wall || (kp.mask != nullptr && kp.mask[gy * nx + gxb] != 0);
+    }
+    const bool ring_row = ry >= 1 && ry <= TY + 2;
+    if (ring_row && ((sa && rx >= 1 && rx <= TX + 2) || (sb && rx + 1 >= 1 && rx + 1 <= TX + 2))) ring_solid = 1;
+    CompSums<C> a1{}, a2{}, b1{}, b2{};
+    if (!sa && !sb && gxb == gxa + 1 && (gxa & 1) == 0) {
+      // pitch and plane are even, so the pair starts on an 8-byte boundary
+      const float2* src = reinterpret_cast<const float2*>(fin + (gy * pitch + gxa));
+      const int pl2 = plane >> 1;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        C fa[9], fb[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          const float2 u = ld_pop2<CG>(src + (9 * c + i) * pl2);
+          fa[i] = C(u.x);
+          fb[i] = C(u.y);
+        }
+        (c == 0 ? a1 : a2) = comp_sums<C>(fa);
+        (c == 0 ? b1 : b2) = comp_sums<C>(fb);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (k == 0 ? sa : sb) continue;
+        const SF<S>* src = fin + (gy * pitch + (k == 0 ? gxa : gxb));
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          C f[9];
+#pragma unroll
+          for (int i = 0; i < 9; ++i) f[i] = C(ld_pop<CG>(src + (9 * c + i) * plane));
+          (k == 0 ? (c == 0 ? a1 : a2) : (c == 0 ? b1 : b2)) = comp_sums<C>(f);
+        }
+      }
+    }
+    if (sa) phase_a_wall<C, TX, TY, false>(sm, kp, rx, ry);
+    else phase_a_store<C, SHIFT, TX, TY, false>(sm, kp, rx, ry, a1, a2);
+    if (sb) phase_a_wall<C, TX, TY, false>(sm, kp, rx + 1, ry);
+    else phase_a_store<C, SHIFT, TX, TY, false>(sm, kp, rx + 1, ry, b1, b2);
+  }
+  return ring_solid;
+}
+
 // Phase A on one tile: rho, psi (and T for the observables) on the tile + 2-node ring.
 // Returns (CTA-uniform) whether the fast path applies.
 template <class S, class C, bool SHIFT, bool NEED_T, int TX, int TY, int NT, bool CG>
@@ -191,6 +314,10 @@ __device__ __forceinline__ bool tile_phase_a(const SF<S>* __restrict__ fin, cons
   const bool small_x = nx < TX + 4, small_y = ny < TY + 4;
   const C rb0 = SHIFT ? kp.rho_bar[0] : C(0), rb1 = SHIFT ? kp.rho_bar[1] : C(0);
   int ring_solid = 0;
+  constexpr bool kPairs = !NEED_T && sizeof(SF<S>) == 4 && (RX % 2 == 0);
+  if constexpr (kPairs) {
+    ring_solid = tile_phase_a_pairs<S, C, SHIFT, TX, TY, NT, CG>(fin, kp, x0, y0, sm, tid);
+  } else
   for (int r = tid; r < RX * RY; r += NT) {
     const int ry = r / RX, rx = r - ry * RX;
     int gx = x0 + rx - 2;

@@ -96,6 +96,34 @@ def test_fp64_small_and_ragged_lattices(nx, ny, periodic, posts):
     assert og["n_fluid"] == oo["n_fluid"]
 
 
+@pytest.mark.parametrize("precision", [lb.LB_FP32_SHIFTED, lb.LB_FP32_FP16T])
+@pytest.mark.parametrize("nx,ny,periodic,posts", [(37, 21, 0, True), (5, 7, 0, False), (33, 12, 1, False),
+                                                  (129, 40, 0, True)])
+def test_fp32_forms_small_odd_and_ragged_lattices(precision, nx, ny, periodic, posts):
+    """FP32 storage on lattices narrower than a tile and of odd width (periodic wraps that split a
+    pair of region nodes, posts on both walls): rho and T stay within the FP32 (FP16 thermal) bound
+    of the FP64 oracle and mass is conserved."""
+    if periodic:
+        y, x = np.mgrid[0:ny, 0:nx]
+        r1 = np.where((x - nx / 2) ** 2 + (y - ny / 2) ** 2 < (min(nx, ny) / 4) ** 2, 1.4, 0.1)
+        params = dict(I.EMULSION_PARAMS, nx=nx, ny=ny, periodic_y=1, T_down=0.0, T_up=0.0, alpha_g=1e-4)
+        T0 = 0.1 * np.sin(2 * np.pi * x / nx)
+        r2, mask = 1.5 - r1, None
+    else:
+        w = I.emulsion_small(nx=nx, ny=ny, n_drops=1, R=max(min(nx, ny) / 5.0, 1.5))
+        params, r1, r2, T0 = dict(w.params, alpha_g=1e-3), w.rho1, w.rho2, w.T0
+        mask = I.posts_mask(nx, ny, 2, 3, 7) if posts else None
+    g, o = _pair(params, r1, r2, T0, mask=mask, precision=precision)
+    g.step(60)
+    o.step(60)
+    fg, fo = g.fields(), o.fields()
+    for k in ("rho1", "rho2"):
+        assert _norm_rel(fg[k], fo[k]) <= 1e-4, (k, _norm_rel(fg[k], fo[k]))
+    tolT = 1e-4 if precision == lb.LB_FP32_SHIFTED else FP16T_T_TOL
+    assert np.abs(fg["T"] - fo["T"]).max() <= tolT * max(np.abs(fo["T"]).max(), 0.5)
+    np.testing.assert_allclose(g.observables()["mass"], o.observables()["mass"], rtol=1e-6)
+
+
 def test_graph_replay_equals_single_launches_bitwise():
     """lb_step(n) replays 16-step CUDA graphs plus single launches; the result is bit-identical
     whatever the split (the kernel is deterministic)."""
