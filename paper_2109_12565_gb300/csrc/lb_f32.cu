@@ -33,20 +33,21 @@ const Cand kCands[] = {
 constexpr int kPlain = (int)(sizeof kCands / sizeof kCands[0]);
 
 // Candidates 0 .. kPlain-1: the plain tile kernel; then the TMA-fed pipelined tile kernel (lb_tma.cu);
-// then the strip-marching kernel (lb_stream.cu).  A TMA candidate that does not apply to the lattice
-// runs candidate 0 instead.
+// then the strip-marching kernel (lb_stream.cu).  A candidate that does not apply to the lattice runs
+// candidate 0 instead.
 int tile_count_f32() { return kPlain + tma_count_f32() + stream_count_f32(); }
 TileChoice tile_info_f32(int k) {
   if (k < kPlain) return kCands[k].t;
-  if (k < kPlain + tma_count_f32()) return tma_info_f32(k - kPlain);
-  return stream_info_f32(k - kPlain - tma_count_f32());
+  k -= kPlain;
+  if (k < tma_count_f32()) return tma_info_f32(k);
+  return stream_info_f32(k - tma_count_f32());
 }
 cudaError_t launch_step_tile_f32(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s) {
   if (k < kPlain) return kCands[k].fn(c, fin, fout, s);
-  const cudaError_t e = k < kPlain + tma_count_f32() ? launch_step_tma_f32(k - kPlain, c, fin, fout, s)
-                                                      : launch_step_stream_f32(k - kPlain - tma_count_f32(), c, fin, fout, s);
-  if (e == cudaErrorNotSupported) return kCands[0].fn(c, fin, fout, s);
-  return e;
+  k -= kPlain;
+  const cudaError_t e = k < tma_count_f32() ? launch_step_tma_f32(k, c, fin, fout, s)
+                                            : launch_step_stream_f32(k - tma_count_f32(), c, fin, fout, s);
+  return e == cudaErrorNotSupported ? kCands[0].fn(c, fin, fout, s) : e;
 }
 
 cudaError_t init_f32(const StepCfg& c, const double* fields, void* buf, cudaStream_t s) {
