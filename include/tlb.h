@@ -77,6 +77,10 @@ typedef struct lb_params {
   double body_fx;      /* constant x acceleration on both components (0 in the paper's runs) */
   double shift_rho[2]; /* FP32 forms: rho_bar_l; NaN = mean initial density of the fluid nodes */
   double shift_T;      /* FP32 forms: T_bar; NaN = (T_down + T_up) / 2 */
+  double u_wall[2];    /* x velocity of the flat bottom / top wall (Couette rheology, Sec. 2.2 and 3.2.1):
+                          a population bounced off a moving wall row gains 6 w_i rho_l c_ix u_wall
+                          (mass-conserving); obstacle posts stay at rest.  0 = resting walls.  The
+                          adjoint needs resting walls. */
 } lb_params;
 
 /* Observables of the current state S_t (pre-collision populations at step t). */
@@ -92,6 +96,10 @@ typedef struct lb_obs {
   long long n_bad;     /* fluid nodes with a non-finite or non-positive density or non-finite T */
   int status;          /* LB_OK, or LB_EUNSTABLE when n_bad > 0 */
   int _pad;
+  double wall_fx[2];   /* x momentum the next step hands to the bottom / top wall row through its
+                          bounce-back links, sum over both components of c_ix (f*_i + f_bounced): the
+                          force of the fluid on each flat wall per time step; in a steady Couette
+                          flow -wall_fx[1] / nx is the shear stress.  0 when periodic_y. */
 } lb_obs;
 
 typedef struct lb_handle lb_handle;
@@ -167,8 +175,8 @@ int lb_tile_info(const lb_handle* h, int candidate, int* tx, int* ty, int* threa
  * bytes or NULL, as the mask given to lb_init.  out: host struct, filled before return (step = 0).
  * stream: cudaStream_t or NULL; the call synchronises it.
  * Scratch: a 2 MiB file-scope device array that every GPU loading the library holds until exit;
- * lattices needing more than 26,212 tiles of 32 x 16 nodes are rejected with LB_EINVAL before any
- * launch (4096 x 3264 fits, 4096 x 3280 does not).  The first call on a device looks the array up
+ * lattices needing more than 21,844 tiles of 32 x 16 nodes are rejected with LB_EINVAL before any
+ * launch (4096 x 2720 fits, 4096 x 2736 does not).  The first call on a device looks the array up
  * (cudaGetSymbolAddress) and must come before any stream capture.  All calls on a device share the
  * array: calls that overlap on the GPU race and must be serialised by the caller.  Allocates
  * nothing.  Returns LB_OK, LB_EUNSTABLE (out filled), LB_EINVAL or LB_ECUDA; lb_last_error is not

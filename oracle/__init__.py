@@ -34,11 +34,12 @@ class OrcParams(ctypes.Structure):
         ("T_up", ctypes.c_double),
         ("alpha_g", ctypes.c_double),
         ("body_fx", ctypes.c_double),
+        ("u_wall", ctypes.c_double * 2),
     ]
 
 
 _PARAM_KEYS = ("nx", "ny", "periodic_y", "tau", "tau_g", "rho0", "G12", "Ga", "Gr", "rho_wall",
-               "T_down", "T_up", "alpha_g", "body_fx")
+               "T_down", "T_up", "alpha_g", "body_fx", "u_wall")
 
 
 def lib(omp=False):
@@ -57,6 +58,7 @@ def lib(omp=False):
         L.orc_run.argtypes = [P, u8, dp, dp, ctypes.c_long]
         L.orc_fields.argtypes = [P, u8, dp, dp, dp, dp, dp, dp]
         L.orc_observables.argtypes = [P, u8, dp, dp]
+        L.orc_wall_force.argtypes = [P, u8, dp, dp]
         L.orc_adjoint_step.argtypes = [P, u8, dp, dp, ctypes.c_double, dp, dp]
         L.orc_adjoint_run.argtypes = [P, u8, dp, dp, dp, ctypes.c_long, dp, dp, dp]
         ip = ctypes.POINTER(ctypes.c_int)
@@ -65,7 +67,7 @@ def lib(omp=False):
         L.orc_digital_voronoi.argtypes = [P, u8, dp, dp, ctypes.c_int, ip]
         L.orc_voronoi_links.argtypes = [P, ip, ip, ctypes.c_long, ctypes.POINTER(ctypes.c_long)]
         for f in ("orc_solid_map", "orc_init", "orc_forces", "orc_step", "orc_run", "orc_fields",
-                  "orc_observables", "orc_adjoint_step", "orc_adjoint_run", "orc_droplet_labels",
+                  "orc_observables", "orc_wall_force", "orc_adjoint_step", "orc_adjoint_run", "orc_droplet_labels",
                   "orc_droplet_centres", "orc_digital_voronoi", "orc_voronoi_links"):
             getattr(L, f).restype = ctypes.c_int
         _LIBS[key] = L
@@ -79,7 +81,7 @@ def make_params(p):
         if k not in p:
             continue
         v = p[k]
-        if k in ("Ga", "Gr", "rho_wall"):
+        if k in ("Ga", "Gr", "rho_wall", "u_wall"):
             getattr(s, k)[0] = float(v[0])
             getattr(s, k)[1] = float(v[1])
         elif k in ("nx", "ny", "periodic_y"):
@@ -161,8 +163,10 @@ class Oracle:
         out = np.zeros(8)
         _check(self.L.orc_observables(ctypes.byref(self.cp), self._mask_ptr, _dp(self.state), _dp(out)),
                "observables")
+        wf = np.zeros(2)
+        _check(self.L.orc_wall_force(ctypes.byref(self.cp), self._mask_ptr, _dp(self.state), _dp(wf)), "wall_force")
         return {"mass": out[0:2].copy(), "mom": out[2:4].copy(), "Nu": out[4], "E": out[5], "n_bad": int(out[6]),
-                "n_fluid": int(out[7])}
+                "n_fluid": int(out[7]), "wall_fx": wf}
 
     def solid(self):
         s = np.zeros((self.ny, self.nx), dtype=np.uint8)

@@ -265,7 +265,17 @@ static double equilibrium(int i, double a, double ux, double uy) {
   return weight_w(i) * a * (1.0 + cu / cs2 + cu * cu / (2.0 * cs2 * cs2) - uu / (2.0 * cs2));
 }
 
-int orc_step(const orc_params* prm, const uint8_t* mask, const double* in, double* out) {
+/* x velocity of the wall that solid row yd belongs to: the flat bottom / top wall rows move with
+ * u_wall (Couette, Sec. 2.2); obstacle posts and periodic lattices are at rest. */
+static double wall_u(const orc_params* prm, int yd) {
+  if (prm->periodic_y) return 0.0;
+  if (yd == 0) return prm->u_wall[0];
+  if (yd == prm->ny - 1) return prm->u_wall[1];
+  return 0.0;
+}
+
+/* One step; with wall_fx != NULL also the x momentum handed to the bottom / top wall rows. */
+static int step_impl(const orc_params* prm, const uint8_t* mask, const double* in, double* out, double* wall_fx) {
   if (!valid(prm)) return -1;
   const int nx = prm->nx, ny = prm->ny;
   const long N = (long)nx * ny;
@@ -281,6 +291,7 @@ int orc_step(const orc_params* prm, const uint8_t* mask, const double* in, doubl
   forces_from_fields(prm, solid, rho1, rho2, T, F);
 
   memset(out, 0, sizeof(double) * 27 * (size_t)N);
+  double* rowacc = (double*)calloc(2 * (size_t)ny, sizeof(double)); /* per row: bottom, top wall */
 #pragma omp parallel for schedule(static)
   for (int y = 0; y < ny; ++y) {
     for (int x = 0; x < nx; ++x) {
@@ -319,17 +330,46 @@ int orc_step(const orc_params* prm, const uint8_t* mask, const double* in, doubl
           out[(long)(9 + i) * N + nd] = fpost[9 + i];
           out[(long)(18 + i) * N + nd] = fpost[18 + i];
         } else {
+          /* a moving flat wall gives the bounced population of component l the momentum
+           * 2 w_i rho_l (c_i . u_w) / c_s^2 = 6 w_i rho_l c_ix u_w (mass-conserving: the links
+           * that cross a flat wall have sum_i w_i c_ix = 0); posts and resting walls add nothing */
           const int o = OPP[i];
-          out[(long)o * N + n] = fpost[i];
-          out[(long)(9 + o) * N + n] = fpost[9 + i];
+          const double uw = wall_u(prm, yd);
+          const double b1 = fpost[i] - 6.0 * weight_w(i) * r[0] * CX[i] * uw;
+          const double b2 = fpost[9 + i] - 6.0 * weight_w(i) * r[1] * CX[i] * uw;
+          out[(long)o * N + n] = b1;
+          out[(long)(9 + o) * N + n] = b2;
           out[(long)(18 + o) * N + n] = -fpost[18 + i] + 2.0 * weight_w(i) * wall_T(prm, yd);
+          if (!prm->periodic_y && (yd == 0 || yd == ny - 1))
+            rowacc[2 * y + (yd == 0 ? 0 : 1)] += CX[i] * ((fpost[i] + b1) + (fpost[9 + i] + b2));
         }
       }
     }
   }
+  if (wall_fx) {
+    wall_fx[0] = wall_fx[1] = 0.0;
+    for (int y = 0; y < ny; ++y) {
+      wall_fx[0] += rowacc[2 * y];
+      wall_fx[1] += rowacc[2 * y + 1];
+    }
+  }
+  free(rowacc);
   free(buf);
   free(solid);
   return 0;
+}
+
+int orc_step(const orc_params* prm, const uint8_t* mask, const double* in, double* out) {
+  return step_impl(prm, mask, in, out, NULL);
+}
+
+int orc_wall_force(const orc_params* prm, const uint8_t* mask, const double* state, double* out) {
+  if (!valid(prm) || !out) return -1;
+  double* tmp = (double*)malloc(sizeof(double) * 27 * (size_t)prm->nx * prm->ny);
+  if (!tmp) return -2;
+  const int rc = step_impl(prm, mask, state, tmp, out);
+  free(tmp);
+  return rc;
 }
 
 int orc_run(const orc_params* prm, const uint8_t* mask, double* state, double* work, long nsteps) {

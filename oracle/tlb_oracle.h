@@ -50,6 +50,7 @@ typedef struct orc_params {
   double T_down, T_up; /* bottom / top wall temperatures, Sec. 3.2.3 */
   double alpha_g;   /* buoyancy coefficient alpha*g, Eq. (alphaG) */
   double body_fx;   /* constant x-acceleration (Poiseuille pin only; 0 in the paper's runs) */
+  double u_wall[2]; /* x velocity of the bottom / top flat wall (Couette, Sec. 2.2); posts rest */
 } orc_params;
 
 /* Velocity tables: c[25][2], w[9] (D2Q9 weights), p[25] (two-belt weights of Fig. 1b). */
@@ -70,6 +71,11 @@ int orc_forces(const orc_params* prm, const uint8_t* mask, const double* rho1, c
 /* One time step S_t -> S_{t+1}: moments, pseudo-potentials, forces, shifted velocities, BGK
  * collision, streaming with half-way bounce-back (fluid) and anti-bounce-back (thermal). */
 int orc_step(const orc_params* prm, const uint8_t* mask, const double* in, double* out);
+
+/* x momentum that the step from S_t hands to the bottom (out[0]) and top (out[1]) flat walls through
+ * their bounce-back links, sum over both components of c_ix (f*_i + f_bounced); the force of the fluid
+ * on each wall per time step.  0 when periodic in y. */
+int orc_wall_force(const orc_params* prm, const uint8_t* mask, const double* state, double* out);
 
 /* nsteps steps in place; work must hold 27*nx*ny doubles. */
 int orc_run(const orc_params* prm, const uint8_t* mask, double* state, double* work, long nsteps);

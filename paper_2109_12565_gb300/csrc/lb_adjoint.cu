@@ -37,12 +37,14 @@ using namespace tlb;
 
 namespace tlb {
 
+// Tile of the reverse-step kernels and the resident CTAs per SM asked of the compiler: FP32 fits 80
+// registers without spills at 3 CTAs per SM; FP64 needs its ~240 registers (a cap spills).
 template <class S> struct AdjTile;
-template <> struct AdjTile<double> { static constexpr int TX = 32, TY = 16, BY = 8; };
-template <> struct AdjTile<float> { static constexpr int TX = 64, TY = 16, BY = 4; };
+template <> struct AdjTile<double> { static constexpr int TX = 32, TY = 16, BY = 8, MINB = 1; };
+template <> struct AdjTile<float> { static constexpr int TX = 32, TY = 16, BY = 8, MINB = 3; };
 
-template <class S, class C, bool SHIFT, int TX, int TY, int BY>
-__global__ void __launch_bounds__(TX * BY, 1)
+template <class S, class C, bool SHIFT, int TX, int TY, int BY, int MINB>
+__global__ void __launch_bounds__(TX * BY, MINB)
 lb_adj1_kernel(const S* __restrict__ fin, const S* __restrict__ lam_out, S* __restrict__ lam_in,
                S* __restrict__ lamF, const KParams<C> kp, const C cJ, const C nuc, const double mirror_coef,
                double* __restrict__ acc) {
@@ -222,8 +224,8 @@ template <class C, int TX, int TY> struct Adj2Smem {
   unsigned char solid[TY][TX];
 };
 
-template <class S, class C, bool SHIFT, int TX, int TY, int BY>
-__global__ void __launch_bounds__(TX * BY, 1)
+template <class S, class C, bool SHIFT, int TX, int TY, int BY, int MINB>
+__global__ void __launch_bounds__(TX * BY, MINB)
 lb_adj2_kernel(const S* __restrict__ fin, const S* __restrict__ lamF, S* __restrict__ lam_in, const KParams<C> kp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto& sm = *reinterpret_cast<Adj2Smem<C, TX, TY>*>(smem_raw);
@@ -356,12 +358,20 @@ cudaError_t adj_step_impl(const StepCfg& c, const void* S_t, const void* lam_out
   using T = AdjTile<S>;
   const dim3 grid = grid_for(c.nx, c.ny, T::TX, T::TY), block(T::TX, T::BY, 1);
   const KParams<S> kp = make_kparams<S>(c);
-  auto k1 = lb_adj1_kernel<S, S, SHIFT, T::TX, T::TY, T::BY>;
-  auto k2 = lb_adj2_kernel<S, S, SHIFT, T::TX, T::TY, T::BY>;
+  auto k1 = lb_adj1_kernel<S, S, SHIFT, T::TX, T::TY, T::BY, T::MINB>;
+  auto k2 = lb_adj2_kernel<S, S, SHIFT, T::TX, T::TY, T::BY, T::MINB>;
   constexpr size_t b1 = sizeof(TileSmem<S, T::TX, T::TY, false>), b2 = sizeof(Adj2Smem<S, T::TX, T::TY>);
-  cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2);
+  static std::atomic<unsigned long long> done{0};  // shared-memory opt-in set once per device ordinal (mod 64)
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(done.load() & bit)) {
+    e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2);
+    if (e != cudaSuccess) return e;
+    done.fetch_or(bit);
+  }
   k1<<<grid, block, b1, s>>>(static_cast<const S*>(S_t), static_cast<const S*>(lam_out), static_cast<S*>(lam_in),
                              static_cast<S*>(lamF), kp, S(cJ), S(nuc), mirror_coef, acc);
   e = cudaGetLastError();
@@ -501,6 +511,7 @@ int lb_adjoint_step(lb_handle* h, const void* d_lam_next, void* d_lam, double cJ
                     double* dJ_dTdown) {
   if (!h || !d_lam || !d_adj_ws) return LB_EINVAL;
   if (h->p.precision == LB_FP32_FP16T) return afail(h, LB_EINVAL, "the adjoint needs LB_FP64 or LB_FP32_SHIFTED");
+  if (h->cfg.u_wall[0] != 0.0 || h->cfg.u_wall[1] != 0.0) return afail(h, LB_EINVAL, "the adjoint needs resting walls");
   const AdjLayout A = adj_layout(h, 1, 1);
   if (adj_bytes < A.total || ((uintptr_t)d_adj_ws % kAlign) != 0) return afail(h, LB_ENOSPACE, "adjoint workspace too small");
   unsigned char* ws = static_cast<unsigned char*>(d_adj_ws);
@@ -532,6 +543,7 @@ int lb_adjoint(lb_handle* h, int n_steps, int ckpt_every, void* d_adj_ws, size_t
                double* dJ_dTdown) {
   if (!h || n_steps < 1 || ckpt_every < 1 || !d_adj_ws || !J) return LB_EINVAL;
   if (h->p.precision == LB_FP32_FP16T) return afail(h, LB_EINVAL, "the adjoint needs LB_FP64 or LB_FP32_SHIFTED");
+  if (h->cfg.u_wall[0] != 0.0 || h->cfg.u_wall[1] != 0.0) return afail(h, LB_EINVAL, "the adjoint needs resting walls");
   const AdjLayout A = adj_layout(h, n_steps, ckpt_every);
   if (adj_bytes < A.total || ((uintptr_t)d_adj_ws % kAlign) != 0) return afail(h, LB_ENOSPACE, "adjoint workspace too small");
   unsigned char* ws = static_cast<unsigned char*>(d_adj_ws);

@@ -247,6 +247,8 @@ int lb_observables(lb_handle* h, lb_obs* out) {
   out->step = h->step;
   out->status = out->n_bad > 0 ? LB_EUNSTABLE : LB_OK;
   out->_pad = 0;
+  out->wall_fx[0] = v[10];
+  out->wall_fx[1] = v[11];
   if (out->status != LB_OK) return fail(h, LB_EUNSTABLE, "%lld fluid nodes with non-finite or non-positive density", out->n_bad);
   return LB_OK;
 }

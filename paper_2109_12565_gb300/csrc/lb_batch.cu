@@ -605,6 +605,8 @@ int lb_batch_observables(lb_batch* b, int r, lb_obs* out) {
   out->step = b->step;
   out->status = out->n_bad > 0 ? LB_EUNSTABLE : LB_OK;
   out->_pad = 0;
+  out->wall_fx[0] = v[10];
+  out->wall_fx[1] = v[11];
   return out->status;
 }
 

@@ -10,7 +10,7 @@ namespace tlb {
 enum Mode : int { MODE_STEP = 0, MODE_OBS = 1, MODE_FIELDS = 2 };
 
 // Number of doubles each block writes to the partial-sum buffer in MODE_OBS.
-constexpr int kObsSlots = 10;
+constexpr int kObsSlots = 12;
 // Final observable vector written by the reduction kernel.
 constexpr int kObsOut = 16;
 
@@ -33,6 +33,7 @@ struct StepCfg {
   double rho_bar[2], T_bar;   // storage shifts (0 in FP64)
   double kappa;               // (tau_g - 1/2) / 3, Eq. K
   double H;                   // wall-to-wall height ny - 2
+  double u_wall[2];           // x velocity of the bottom / top flat wall rows (Couette)
   int* err;                   // device error word for bounded waits (nullptr: kernels that wait are not used)
 };
 

@@ -84,6 +84,8 @@ __global__ void __launch_bounds__(256) lb_obs_finalize_kernel(const double* __re
     out[7] = nf;
     out[8] = t[4];
     out[9] = t[5];
+    out[10] = t[9];   // x momentum to the bottom wall per step
+    out[11] = t[10];  // x momentum to the top wall per step
   }
 }
 

@@ -35,7 +35,8 @@ inline const char* check_params(const lb_params* p) {
   if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return "tau must be finite and > 1/2";
   if (!(p->tau_g > 0.5) || !std::isfinite(p->tau_g)) return "tau_g must be finite and > 1/2";
   if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0)) return "rho0 must be finite and > 0";
-  const double vals[] = {p->G12, p->Ga[0], p->Ga[1], p->Gr[0], p->Gr[1], p->T_down, p->T_up, p->alpha_g, p->body_fx};
+  const double vals[] = {p->G12,    p->Ga[0],  p->Ga[1],   p->Gr[0],      p->Gr[1],      p->T_down,
+                         p->T_up,   p->alpha_g, p->body_fx, p->u_wall[0], p->u_wall[1]};
   for (double v : vals)
     if (!std::isfinite(v)) return "coupling, temperature and force parameters must be finite";
   if (!(p->rho_wall[0] > 0.0) || !(p->rho_wall[1] > 0.0) || !std::isfinite(p->rho_wall[0]) ||
@@ -113,6 +114,8 @@ inline StepCfg make_stepcfg(const lb_params& p, int pitch, const uint8_t* d_mask
   }
   c.kappa = (p.tau_g - 0.5) / 3.0;
   c.H = (double)(p.ny - 2);
+  c.u_wall[0] = p.periodic_y ? 0.0 : p.u_wall[0];
+  c.u_wall[1] = p.periodic_y ? 0.0 : p.u_wall[1];
   return c;
 }
 

@@ -89,6 +89,7 @@ template <class C> struct KParams {
   int tau_is_one;          // tau == 1: f* = f^eq exactly, the relaxation is skipped
   int tau_g_is_one;        // tau_g == 1: g* = g^eq
   double rho_w_d[2], T_down_d, T_up_d;  // field output at solid nodes
+  C uw6[2];                // 6 u_wall of the bottom / top wall row (moving-wall bounce-back)
 };
 
 template <class C> inline KParams<C> make_kparams(const StepCfg& c) {
@@ -128,6 +129,8 @@ template <class C> inline KParams<C> make_kparams(const StepCfg& c) {
   k.tau_g_is_one = (c.inv_tau_g == 1.0) ? 1 : 0;
   k.T_down_d = c.T_down;
   k.T_up_d = c.T_up;
+  k.uw6[0] = C(6.0 * c.u_wall[0]);
+  k.uw6[1] = C(6.0 * c.u_wall[1]);
   return k;
 }
 
@@ -494,11 +497,13 @@ __device__ __forceinline__ void node_collide(const KParams<C>& kp, const C f[9],
 
 // Streaming (push) of the 27 post-collision populations of fluid node (gx, gy) (row-major index idx in
 // the padded buffer) with half-way bounce-back of f and thermal anti-bounce-back of g where x + c_i is
-// solid (Sec. 2.2).  solid[cy + c_iy][cx + c_ix] is the solid flag of x + c_i in the caller's
+// solid (Sec. 2.2).  A link into a moving flat wall row also takes 6 w_i rho_l c_ix u_wall (r1, r2:
+// the node's densities).  solid[cy + c_iy][cx + c_ix] is the solid flag of x + c_i in the caller's
 // shared-memory view.  FAST: no solid node around and no periodic wrap, every store is a constant offset.
 template <class S, class C, bool FAST, int RX>
 __device__ __forceinline__ void push_store(SF<S>* __restrict__ fout, const KParams<C>& kp, int idx, int gx, int gy,
-                                           const C post[27], const unsigned char (*solid)[RX], int cx, int cy) {
+                                           const C post[27], const unsigned char (*solid)[RX], int cx, int cy, C r1,
+                                           C r2) {
   using F = SF<S>;
   using G = SG<S>;
   const int nx = kp.nx, ny = kp.ny, pitch = kp.pitch, plane = kp.plane;
@@ -527,9 +532,16 @@ __device__ __forceinline__ void push_store(SF<S>* __restrict__ fout, const KPara
         gout[i * plane + didx] = down<G>(post[18 + i]);
       } else {
         const int o = oppq(i);
-        const C twoTw = (2 * (gy + cyq(i)) < ny) ? kp.twoTw_down : kp.twoTw_up;
-        fout[o * plane + idx] = down<F>(post[i]);
-        fout[(9 + o) * plane + idx] = down<F>(post[9 + i]);
+        const int ys = gy + cyq(i);
+        const C twoTw = (2 * ys < ny) ? kp.twoTw_down : kp.twoTw_up;
+        C m1 = C(0), m2 = C(0);
+        if (cxq(i) != 0 && !kp.periodic_y && (ys == 0 || ys == ny - 1)) {
+          const C wc = wq<C>(i) * C(cxq(i)) * (ys == 0 ? kp.uw6[0] : kp.uw6[1]);
+          m1 = wc * r1;
+          m2 = wc * r2;
+        }
+        fout[o * plane + idx] = down<F>(post[i] - m1);
+        fout[(9 + o) * plane + idx] = down<F>(post[9 + i] - m2);
         gout[o * plane + idx] = down<G>(-post[18 + i] + wq<C>(i) * twoTw);
       }
     }
@@ -606,6 +618,23 @@ __device__ __forceinline__ void tile_phase_b(const Src& pop, SF<S>* __restrict__
                        !isfinite((double)T);
       acc[7] += bad ? 1.0 : 0.0;
       acc[8] += 1.0;
+      // x momentum the next step hands to a flat wall row through the bounce-back links of this node
+      // (momentum exchange, c_ix (f* + f_bounced) per component).  In shifted storage the
+      // 2 w_i rho_bar c_ix terms of the two diagonal links cancel, so deviations suffice.
+      if (!kp.periodic_y && (gy == 1 || gy == ny - 2)) {
+        C post[27];
+        node_collide<C, SHIFT>(kp, f, h, g, r1, r2, dr1, dr2, T, dT, ux, uy, i1, i2, Fx, Fy, uHx, uHy, post);
+        double wsum = 0.0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          const int ys = gy + cyq(i);
+          if (cxq(i) == 0 || (ys != 0 && ys != ny - 1)) continue;
+          const C wc = wq<C>(i) * C(cxq(i)) * (ys == 0 ? kp.uw6[0] : kp.uw6[1]);
+          const C b1 = post[i] - wc * r1, b2 = post[9 + i] - wc * r2;
+          wsum += (double)cxq(i) * (((double)post[i] + (double)b1) + ((double)post[9 + i] + (double)b2));
+        }
+        acc[gy == 1 ? 9 : 10] += wsum;
+      }
     } else if constexpr (MODE == MODE_FIELDS) {
       const long long n = (long long)gy * nx + gx, N = (long long)nx * ny;
       aux[n] = (double)r1;
@@ -616,7 +645,7 @@ __device__ __forceinline__ void tile_phase_b(const Src& pop, SF<S>* __restrict__
     } else {
       C post[27];
       node_collide<C, SHIFT>(kp, f, h, g, r1, r2, dr1, dr2, T, dT, ux, uy, i1, i2, Fx, Fy, uHx, uHy, post);
-      push_store<S, C, FAST>(fout, kp, idx, gx, gy, post, sm.solid, cx, cy);
+      push_store<S, C, FAST>(fout, kp, idx, gx, gy, post, sm.solid, cx, cy, r1, r2);
     }
   }
 }

@@ -75,7 +75,7 @@ extern "C" int lb_observables_static(const lb_params* p, const double* d_state, 
   if (d_mask && p->periodic_y) return LB_EINVAL;
   if (!(p->tau > 0.5) || !(p->tau_g > 0.5) || !(p->rho0 > 0.0) || !(p->rho_wall[0] > 0.0) || !(p->rho_wall[1] > 0.0) ||
       !finite_all({p->tau, p->tau_g, p->rho0, p->G12, p->Ga[0], p->Ga[1], p->Gr[0], p->Gr[1], p->rho_wall[0],
-                   p->rho_wall[1], p->T_down, p->T_up, p->alpha_g, p->body_fx}))
+                   p->rho_wall[1], p->T_down, p->T_up, p->alpha_g, p->body_fx, p->u_wall[0], p->u_wall[1]}))
     return LB_EINVAL;
   const dim3 grid = grid_for(p->nx, p->ny, Tile<double>::TX, Tile<double>::TY);
   const long long n_blocks = (long long)grid.x * grid.y;
@@ -114,6 +114,8 @@ extern "C" int lb_observables_static(const lb_params* p, const double* d_state, 
   c.body_fx = p->body_fx;
   c.kappa = (p->tau_g - 0.5) / 3.0;
   c.H = (double)(p->ny - 2);
+  c.u_wall[0] = p->periodic_y ? 0.0 : p->u_wall[0];
+  c.u_wall[1] = p->periodic_y ? 0.0 : p->u_wall[1];
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* final_out = scratch;            // kObsOut slots
@@ -135,5 +137,7 @@ extern "C" int lb_observables_static(const lb_params* p, const double* d_state, 
   out->step = 0;
   out->status = out->n_bad > 0 ? LB_EUNSTABLE : LB_OK;
   out->_pad = 0;
+  out->wall_fx[0] = v[10];
+  out->wall_fx[1] = v[11];
   return out->status;
 }

@@ -84,7 +84,7 @@ __device__ __forceinline__ void stream_node(const float* __restrict__ fin, float
   const float uHy = uy + 0.5f * (Fy[0] + Fy[1]) * inv_rho;
   float post[27];
   node_collide<float, true>(kp, f, h, g, r1, r2, dr1, dr2, T, dT, ux, uy, i1, i2, Fx, Fy, uHx, uHy, post);
-  push_store<float, float, FAST, kSRX>(fout, kp, idx, gx, gy, post, w.solid, cx, cy);
+  push_store<float, float, FAST, kSRX>(fout, kp, idx, gx, gy, post, w.solid, cx, cy, r1, r2);
 }
 
 // Grid: (strips, segments).  Segment s covers row groups [s G / S, (s + 1) G / S) of the G = ceil(ny / 4).

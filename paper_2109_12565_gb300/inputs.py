@@ -73,6 +73,32 @@ def posts_mask(nx, ny, height, width, period):
     return m
 
 
+def rough_wall_mask(nx, ny, height, width, lam, alpha=0.0, asymmetric=False, down=True, up=True, x0=0):
+    """Trapezoidal roughness on the walls (Sec. 5, Fig. roughness a): an obstacle every ``lam``
+    columns starting at column x0, ``height`` rows tall above the wall row (below it on the top wall),
+    ``width`` columns wide at its top; its sides lean outwards by tan(alpha) columns per row towards
+    the wall (alpha in radians from the vertical), the trailing (right) side stays vertical when
+    ``asymmetric``.  alpha = 0 gives rectangular posts.  A node is solid when its column centre lies
+    inside the trapezoid at the row's mid-height.  The top-wall obstacles are the mirror images of
+    the bottom ones in y."""
+    m = np.zeros((ny, nx), dtype=np.uint8)
+    t = float(np.tan(alpha))
+    x = np.arange(nx, dtype=np.float64) + 0.5
+    for k in range(height):
+        # row k above the wall: its mid-height is height - k - 0.5 below the obstacle top
+        spread = t * (height - k - 0.5)
+        rel = (x - x0) % lam
+        left = rel >= lam - spread  # the leaning left side spills into the end of the previous period
+        body = rel < width
+        right = (rel >= width) & (rel < width + (0.0 if asymmetric else spread))
+        row = (left | body | right).astype(np.uint8)
+        if down:
+            m[1 + k, :] |= row
+        if up:
+            m[ny - 2 - k, :] |= row
+    return m
+
+
 def _disk_fields(nx, ny, centres, R):
     """rho1, rho2 with sharp disks of component 1 (x periodic); node (x, y) is inside a disk when
     dx^2 + dy^2 <= R^2 with dx the periodic x distance."""

@@ -42,6 +42,7 @@ class LbParams(ctypes.Structure):
         ("Ga", ctypes.c_double * 2), ("Gr", ctypes.c_double * 2), ("rho_wall", ctypes.c_double * 2),
         ("T_down", ctypes.c_double), ("T_up", ctypes.c_double), ("alpha_g", ctypes.c_double),
         ("body_fx", ctypes.c_double), ("shift_rho", ctypes.c_double * 2), ("shift_T", ctypes.c_double),
+        ("u_wall", ctypes.c_double * 2),
     ]
 
 
@@ -49,7 +50,7 @@ class LbObs(ctypes.Structure):
     _fields_ = [
         ("mass", ctypes.c_double * 2), ("mom", ctypes.c_double * 2), ("Nu", ctypes.c_double), ("E", ctypes.c_double),
         ("step", ctypes.c_longlong), ("n_fluid", ctypes.c_longlong), ("n_bad", ctypes.c_longlong),
-        ("status", ctypes.c_int), ("_pad", ctypes.c_int),
+        ("status", ctypes.c_int), ("_pad", ctypes.c_int), ("wall_fx", ctypes.c_double * 2),
     ]
 
 
@@ -136,7 +137,7 @@ def make_params(p, precision=LB_FP64):
     s.precision = int(p.get("precision", precision))
     for k in ("tau", "tau_g", "rho0", "G12", "T_down", "T_up", "alpha_g", "body_fx"):
         setattr(s, k, float(p.get(k, 0.0)))
-    for k in ("Ga", "Gr", "rho_wall"):
+    for k in ("Ga", "Gr", "rho_wall", "u_wall"):
         v = p.get(k, (0.0, 0.0))
         getattr(s, k)[0], getattr(s, k)[1] = float(v[0]), float(v[1])
     sr = p.get("shift_rho", (math.nan, math.nan))
@@ -213,6 +214,7 @@ class Lattice:
         if rc not in (LB_OK, LB_EUNSTABLE) or (check and rc != LB_OK):
             _check(rc, self._h)
         return {"mass": np.array(o.mass[:]), "mom": np.array(o.mom[:]), "Nu": o.Nu, "E": o.E, "step": o.step,
+                "wall_fx": np.array(o.wall_fx[:]),
                 "n_fluid": o.n_fluid, "n_bad": o.n_bad, "status": o.status}
 
     def fields(self):
@@ -482,6 +484,7 @@ class Batch:
         if rc not in (LB_OK, LB_EUNSTABLE) or (check and rc != LB_OK):
             _bcheck(rc, self._b)
         return {"mass": np.array(o.mass[:]), "mom": np.array(o.mom[:]), "Nu": o.Nu, "E": o.E, "step": o.step,
+                "wall_fx": np.array(o.wall_fx[:]),
                 "n_fluid": o.n_fluid, "n_bad": o.n_bad, "status": o.status}
 
     def fields(self, r):
