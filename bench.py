@@ -190,7 +190,7 @@ def time_form(w, precision, steps, warmup, flush, tile=-1):
     g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, mask=w.mask, precision=precision)
     if tile < 0:
         # the timed steps start with L2 flushed, so the candidates are timed the same way
-        tile, cand_ms = g.autotune(launches=10, scratch=flush[0])
+        tile, cand_ms = g.autotune(launches=30, scratch=flush[0])
     else:
         g.set_tile(tile)
         cand_ms = []
@@ -331,9 +331,18 @@ def cpu_baseline(w, seconds=12.0, min_steps=2):
         n += 1
     dt = time.perf_counter() - t0
     N = w.params["nx"] * w.params["ny"]
+    # the single-threaded build of the same oracle, a shorter sample
+    o1 = O.Oracle(w.params, w.rho1, w.rho2, w.T0, mask=w.mask, omp=False)
+    n1, t1 = 0, time.perf_counter()
+    while n1 < 1 or time.perf_counter() - t1 < seconds / 4:
+        o1.step(1)
+        n1 += 1
+    dt1 = time.perf_counter() - t1
     return {"value": N * n / dt / 1e6, "unit": "MLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]),
             "kind": "oracle", "sample": f"{n} full steps of the {w.name} lattice after 1 untimed step "
-                                        f"({dt:.1f} s, FP64 C oracle, OpenMP over rows)"}
+                                        f"({dt:.1f} s, FP64 C oracle, OpenMP over rows)",
+            "single_thread": {"value": N * n1 / dt1 / 1e6, "unit": "MLUPS", "cores": 1,
+                              "sample": f"{n1} full steps ({dt1:.1f} s, same oracle, single-threaded build)"}}
 
 
 def run_reference(args):
@@ -506,6 +515,7 @@ def main():
         forms["rough_channel_4096x2048"] = {"MLUPS": aggregate_mlups(world, Nr, args.rough_steps, trr),
                                             "ms_per_step": rr["ms_per_step"],
                                             "hbm_frac": achr / peak, "GBps": achr, "steps": args.rough_steps,
+                                            "traffic": _traffic(prof, "rough_channel_fp32", rr["tile"]["candidate"]),
                                             "precision": "fp32_shifted", "Nu": rr["obs"]["Nu"], "tile": rr["tile"]}
     if rdrop:
         step_ms = r32["ms_per_step"] if r32 else None

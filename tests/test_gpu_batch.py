@@ -106,3 +106,27 @@ def test_persistent_wait_timeout_is_reported_not_hung():
     g = lb.Lattice(params[2], r1[2], r2[2], T0[2])
     g.step(3)
     assert g.observables()["n_bad"] == 0
+
+
+def test_full_ensemble_64_replicas_against_oracle():
+    """The 64-replica ensemble (16.5 M nodes, uneven sizes) in the launch configuration the benchmark
+    times (schedule x tile picked by the autotuner), FP32-shifted; three replicas of different sizes
+    checked node by node against the FP64 oracle (OpenMP build) within the FP32 bound."""
+    ens = I.ensemble()
+    b = lb.Batch([w.params for w in ens], [w.rho1 for w in ens], [w.rho2 for w in ens], [w.T0 for w in ens],
+                 precision=lb.LB_FP32_SHIFTED)
+    tune = b.autotune(trial_steps=2)
+    b.step(4)
+    steps = tune["steps_taken"] + 4
+    sizes = [w.params["nx"] * w.params["ny"] for w in ens]
+    picks = sorted({0, int(np.argmin(sizes)), int(np.argmax(sizes))})
+    for r in picks:
+        w = ens[r]
+        o = O.Oracle(w.params, w.rho1, w.rho2, w.T0, omp=True)
+        o.step(steps)
+        fb, fo = b.fields(r), o.fields()
+        for k in ("rho1", "rho2", "T"):
+            rel = np.abs(fb[k] - fo[k]).max() / np.abs(fo[k]).max()
+            assert rel <= 1e-4, (r, k, rel)
+        np.testing.assert_allclose(b.observables(r)["mass"], o.observables()["mass"], rtol=1e-6)
+    b.close()

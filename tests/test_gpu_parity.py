@@ -272,6 +272,25 @@ def test_full_size_1024x512_against_oracle(precision, steps, tol):
             assert _norm_rel(fg[k], fo[k]) <= tol, k
 
 
+def test_rough_channel_4096x2048_full_size_against_oracle():
+    """The 4096 x 2048 rough channel (8.4 M nodes, posts on both walls) in the launch configuration
+    the benchmark times (cold-L2 autotuned tile), FP32-shifted, against the FP64 oracle (OpenMP)."""
+    import torch
+
+    w = I.rough_channel_4096x2048()
+    g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, mask=w.mask, precision=lb.LB_FP32_SHIFTED)
+    scratch = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    g.autotune(launches=2, scratch=scratch)
+    del scratch
+    o = O.Oracle(w.params, w.rho1, w.rho2, w.T0, mask=w.mask, omp=True)
+    g.step(5)
+    o.step(5)
+    fg, fo = g.fields(), o.fields()
+    for k in ("rho1", "rho2", "T"):
+        assert _norm_rel(fg[k], fo[k]) <= 1e-4, k
+    np.testing.assert_allclose(g.observables()["mass"], o.observables()["mass"], rtol=1e-6)
+
+
 def test_unstable_state_is_reported():
     w = I.emulsion_small(nx=16, ny=16, n_drops=1, R=3.0)
     g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0)
