@@ -465,6 +465,85 @@ __global__ void voronoi_colour(Geo g, Grid G, int n_drops, int* __restrict__ col
   col[n] = nearest_centre(g, G, (double)x, (double)y, nullptr);
 }
 
+// Tiled colouring: a CTA of 32 x 8 nodes stages the centres of every cell within 2 cells of the cells
+// its nodes lie in (x periodic; y periodic or clipped) into shared memory, and each node takes the
+// nearest staged centre (same distance arithmetic and tie rule as nearest_centre).  Any centre not
+// staged lies at least 3 cells from the node's own cell, so farther than 2 (conservatively 1) cell
+// edges: a node whose best staged distance is below one cell edge has its exact answer; otherwise
+// (and when the staging list overflows) it runs the full ring search.
+constexpr int kVTX = 32, kVTY = 8, kVList = 1024;
+
+__global__ void __launch_bounds__(kVTX * kVTY) voronoi_tiled(Geo g, Grid G, int n_drops, int* __restrict__ col) {
+  __shared__ double s_x[kVList], s_y[kVList];
+  __shared__ int s_id[kVList];
+  __shared__ int s_n;
+  const int x0 = blockIdx.x * kVTX, y0 = blockIdx.y * kVTY;
+  const int tid = threadIdx.y * kVTX + threadIdx.x;
+  // cell range of the tile's nodes, widened by 2 cells
+  const int x1 = min(x0 + kVTX - 1, g.nx - 1), y1 = min(y0 + kVTY - 1, g.ny - 1);
+  const int cx0 = (int)((double)x0 * G.ncx / g.nx) - 2, cx1 = (int)((double)x1 * G.ncx / g.nx) + 2;
+  const int cy0 = (int)((double)y0 * G.ncy / g.ny) - 2, cy1 = (int)((double)y1 * G.ncy / g.ny) + 2;
+  const int wx = cx1 - cx0 + 1, wy = cy1 - cy0 + 1;
+  if (tid == 0) s_n = 0;
+  __syncthreads();
+  bool overflow = false;
+  for (int c = tid; c < wx * wy; c += kVTX * kVTY) {
+    const int jy = cy0 + c / wx, jx = cx0 + c % wx;
+    int cyi = jy;
+    if (g.periodic_y) cyi = ((jy % G.ncy) + G.ncy) % G.ncy;
+    else if (jy < 0 || jy >= G.ncy) continue;
+    const int cxi = ((jx % G.ncx) + G.ncx) % G.ncx;
+    const int cell = cyi * G.ncx + cxi;
+    const int s = G.cstart[cell], n = G.ccount[cell];
+    if (n == 0) continue;
+    const int at = atomicAdd(&s_n, n);
+    if (at + n > kVList) {
+      overflow = true;
+      continue;
+    }
+    for (int k = 0; k < n; ++k) {
+      const int d = G.citems[s + k];
+      s_id[at + k] = d;
+      s_x[at + k] = G.cx[d];
+      s_y[at + k] = G.cy[d];
+    }
+  }
+  const int any_overflow = __syncthreads_or(overflow ? 1 : 0);
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const long long n = (long long)y * g.nx + x;
+  if (is_solid(g, x, y) || n_drops == 0) {
+    col[n] = -1;
+    return;
+  }
+  const double px = (double)x, py = (double)y;
+  int best_id = -1;
+  double best = 0.0;
+  if (!any_overflow) {
+    const double hx = 0.5 * g.nx, hy = 0.5 * g.ny;
+    const int m = s_n;
+    for (int k = 0; k < m; ++k) {
+      double dx = __dsub_rn(px, s_x[k]);
+      if (dx > hx) dx = __dsub_rn(dx, (double)g.nx);
+      else if (dx < -hx) dx = __dadd_rn(dx, (double)g.nx);
+      double dy = __dsub_rn(py, s_y[k]);
+      if (g.periodic_y) {
+        if (dy > hy) dy = __dsub_rn(dy, (double)g.ny);
+        else if (dy < -hy) dy = __dadd_rn(dy, (double)g.ny);
+      }
+      const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+      const int d = s_id[k];
+      if (best_id < 0 || d2 < best || (d2 == best && d < best_id)) {
+        best = d2;
+        best_id = d;
+      }
+    }
+  }
+  if (any_overflow || best_id < 0 || !(best < G.cw_min * G.cw_min))
+    best_id = nearest_centre(g, G, px, py, nullptr);
+  col[n] = best_id;
+}
+
 // ---------------------------------------------------------------- links (D6)
 
 __device__ __forceinline__ void adj_insert(int* adj, int* deg, int a, int b, int* err) {
@@ -805,7 +884,8 @@ int lb_droplets(lb_handle* h, double threshold, int max_drops, void* d_ws, size_
     cell_fill<<<nb(M, T), T, 0, s>>>(M, v.lcount, v.cstart, v.cfill, v.citems);
   }
   const Grid G = grid_of(v, L, h->p);
-  voronoi_colour<<<nb(N, T), T, 0, s>>>(g, G, M, v.col);
+  voronoi_tiled<<<dim3((unsigned)((h->p.nx + kVTX - 1) / kVTX), (unsigned)((h->p.ny + kVTY - 1) / kVTY)),
+                  dim3(kVTX, kVTY), 0, s>>>(g, G, M, v.col);
   if (M > 0) {
     voronoi_links<<<nb(N, T), T, 0, s>>>(g, v.col, v.adj, v.deg, err);
     adj_sort<<<nb(M, T), T, 0, s>>>(M, v.adj, v.deg, v.lcount);
