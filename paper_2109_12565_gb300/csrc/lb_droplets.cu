@@ -475,6 +475,7 @@ constexpr int kVTX = 32, kVTY = 8, kVList = 1024;
 
 __global__ void __launch_bounds__(kVTX * kVTY) voronoi_tiled(Geo g, Grid G, int n_drops, int* __restrict__ col) {
   __shared__ double s_x[kVList], s_y[kVList];
+  __shared__ float s_xh[kVList], s_xl[kVList], s_yh[kVList], s_yl[kVList];  // two-float split of each centre
   __shared__ int s_id[kVList];
   __shared__ int s_n;
   const int x0 = blockIdx.x * kVTX, y0 = blockIdx.y * kVTY;
@@ -503,9 +504,15 @@ __global__ void __launch_bounds__(kVTX * kVTY) voronoi_tiled(Geo g, Grid G, int 
     }
     for (int k = 0; k < n; ++k) {
       const int d = G.citems[s + k];
+      const double cxd = G.cx[d], cyd = G.cy[d];
+      const float xh = __double2float_rn(cxd), yh = __double2float_rn(cyd);
       s_id[at + k] = d;
-      s_x[at + k] = G.cx[d];
-      s_y[at + k] = G.cy[d];
+      s_x[at + k] = cxd;
+      s_y[at + k] = cyd;
+      s_xh[at + k] = xh;
+      s_xl[at + k] = __double2float_rn(cxd - (double)xh);
+      s_yh[at + k] = yh;
+      s_yl[at + k] = __double2float_rn(cyd - (double)yh);
     }
   }
   const int any_overflow = __syncthreads_or(overflow ? 1 : 0);
@@ -522,7 +529,27 @@ __global__ void __launch_bounds__(kVTX * kVTY) voronoi_tiled(Geo g, Grid G, int 
   if (!any_overflow) {
     const double hx = 0.5 * g.nx, hy = 0.5 * g.ny;
     const int m = s_n;
+    // FP32 screen: node minus the two-float centre is within a few ulps of the exact offset, so
+    // squared distances carry a relative error below 1e-6; only centres within 1e-5 (relative) of the
+    // best screened distance can hold the exact minimum or a tie, and only those are evaluated in
+    // FP64 below with the oracle's arithmetic.
+    const float fx = (float)x, fy = (float)y, fhx = 0.5f * g.nx, fhy = 0.5f * g.ny;
+    auto screen = [&](int k) {
+      float dx = (fx - s_xh[k]) - s_xl[k];
+      if (dx > fhx) dx -= (float)g.nx;
+      else if (dx < -fhx) dx += (float)g.nx;
+      float dy = (fy - s_yh[k]) - s_yl[k];
+      if (g.periodic_y) {
+        if (dy > fhy) dy -= (float)g.ny;
+        else if (dy < -fhy) dy += (float)g.ny;
+      }
+      return dx * dx + dy * dy;
+    };
+    float bf = 3.0e38f;
+    for (int k = 0; k < m; ++k) bf = fminf(bf, screen(k));
+    const float keep = bf * 1.00001f + 1e-3f;
     for (int k = 0; k < m; ++k) {
+      if (screen(k) > keep) continue;
       double dx = __dsub_rn(px, s_x[k]);
       if (dx > hx) dx = __dsub_rn(dx, (double)g.nx);
       else if (dx < -hx) dx = __dadd_rn(dx, (double)g.nx);
