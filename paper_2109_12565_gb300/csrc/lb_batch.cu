@@ -183,6 +183,7 @@ const BatchCand kBatchF32[] = {
     TLB_BATCH_CAND(float, true, 64, 16, 4, 3),
     TLB_BATCH_CAND(float, true, 32, 16, 8, 3),
     TLB_BATCH_CAND(float, true, 128, 16, 2, 3),
+    TLB_BATCH_CAND(float, true, 32, 8, 8, 4),
 };
 const BatchCand kBatchF64[] = {
     TLB_BATCH_CAND(double, false, 32, 16, 8, 2),

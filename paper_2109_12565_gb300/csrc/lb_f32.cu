@@ -27,6 +27,8 @@ const Cand kCands[] = {
     {{32, 16, 8, 4}, launch_step_shape<float, true, 32, 16, 8, 4>},
     {{64, 32, 4, 4}, launch_step_shape<float, true, 64, 32, 4, 4>},
     {{32, 32, 8, 4}, launch_step_shape<float, true, 32, 32, 8, 4>},
+    // one phase-A pass of node pairs and one phase-B node per thread
+    {{32, 8, 8, 4}, launch_step_shape<float, true, 32, 8, 8, 4>},
 };
 }  // namespace
 

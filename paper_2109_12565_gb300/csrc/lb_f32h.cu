@@ -22,6 +22,7 @@ const Cand kCands[] = {
     {{64, 8, 4, 4}, launch_step_shape<F32H16, true, 64, 8, 4, 4>},
     {{64, 32, 8, 2}, launch_step_shape<F32H16, true, 64, 32, 8, 2>},
     {{32, 16, 8, 3}, launch_step_shape<F32H16, true, 32, 16, 8, 3>},
+    {{32, 8, 8, 4}, launch_step_shape<F32H16, true, 32, 8, 8, 4>},
 };
 }  // namespace
 
