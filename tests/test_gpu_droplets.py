@@ -42,7 +42,7 @@ def _compare(g, d, params, mask=None, threshold=BTH):
     return o
 
 
-@pytest.mark.parametrize("precision", [lb.LB_FP64, lb.LB_FP32_SHIFTED])
+@pytest.mark.parametrize("precision", [lb.LB_FP64, lb.LB_FP32_SHIFTED, lb.LB_FP32_FP16T])
 def test_emulsion_64x64_matches_oracle(precision):
     w = I.emulsion_small()
     g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, precision=precision)
@@ -232,3 +232,29 @@ def test_droplet_nusselt_matches_oracle(precision):
     h.step(5)
     dc = h.droplets(BTH)
     np.testing.assert_allclose(h.droplet_nusselt(dc), 1.0, rtol=0, atol=1e-9 if precision == lb.LB_FP64 else 2e-3)
+
+
+def test_compare_reports_the_scratch_it_needs():
+    """lb_droplets_compare with too small a scratch: LB_ENOSPACE and counts4[0] = KiB needed; with that
+    much it succeeds."""
+    import ctypes
+
+    import torch
+
+    w = I.emulsion_small()
+    g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0)
+    a = g.droplets(BTH)
+    g.step(50)
+    b = g.droplets(BTH)
+    counts = (ctypes.c_int * 4)()
+    tiny = torch.empty(256, dtype=torch.uint8, device="cuda")
+    rc = lb.lib().lb_droplets_compare(g._h, ctypes.c_void_p(a["ws"].data_ptr()), ctypes.c_void_p(b["ws"].data_ptr()),
+                                      b["ws_bytes"], 8.0, ctypes.c_void_p(tiny.data_ptr()), 256, counts, None, None,
+                                      None, 0)
+    assert rc == lb.LB_ENOSPACE and counts[0] > 0
+    need = counts[0] * 1024
+    big = torch.empty(need, dtype=torch.uint8, device="cuda")
+    rc = lb.lib().lb_droplets_compare(g._h, ctypes.c_void_p(a["ws"].data_ptr()), ctypes.c_void_p(b["ws"].data_ptr()),
+                                      b["ws_bytes"], 8.0, ctypes.c_void_p(big.data_ptr()), need, counts, None, None,
+                                      None, 0)
+    assert rc == lb.LB_OK and counts[0] == 6
