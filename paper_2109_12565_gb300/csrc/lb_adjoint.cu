@@ -77,8 +77,8 @@ lb_adj1_kernel(const S* __restrict__ fin, const S* __restrict__ lam_out, S* __re
 #pragma unroll
     for (int i = 0; i < 9; ++i) T += C(fin[(18 + i) * plane + idx]);
     T += Tb;
-    const C r1 = sm.rho[0][cy][cx] + (SHIFT ? kp.rho_bar[0] : C(0));
-    const C r2 = sm.rho[1][cy][cx] + (SHIFT ? kp.rho_bar[1] : C(0));
+    const C r1 = sm.rho[cy][cx].x + (SHIFT ? kp.rho_bar[0] : C(0));
+    const C r2 = sm.rho[cy][cx].y + (SHIFT ? kp.rho_bar[1] : C(0));
     const C jx = sm.jx[ty][tx], jy = sm.jy[ty][tx];
     C Fx[2], Fy[2], crx[2], cry[2], sx[2], sy[2], psl[2];
     node_force_parts<C>(sm, kp, cx, cy, r1, r2, T, Fx, Fy, crx, cry, sx, sy, psl);

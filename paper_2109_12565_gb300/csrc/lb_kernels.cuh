@@ -161,7 +161,7 @@ template <> __device__ __forceinline__ double psi_exp<double>(double rho, double
   return rho0 * (1.0 - exp(-rho * inv_rho0));
 }
 template <> __device__ __forceinline__ float psi_exp<float>(float rho, float rho0, float inv_rho0) {
-  return rho0 - rho0 * __expf(-rho * inv_rho0);
+  return __fmaf_rn(-rho0, __expf(__fmul_rn(-rho, inv_rho0)), rho0);  // the same roundings as psi_exp2
 }
 
 // 1 / x: IEEE in FP64, the fast approximate division in FP32.
@@ -175,10 +175,51 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-template <class C, int TX, int TY, bool NEED_T> struct TileSmem {
+// A value per fluid component, interleaved: one 8-byte (FP32) or 16-byte (FP64) shared-memory access
+// reads both components of a node.
+template <class C> struct V2T;
+template <> struct V2T<float> { using type = float2; };
+template <> struct V2T<double> { using type = double2; };
+template <class C> using V2 = typename V2T<C>::type;
+template <class C> __device__ __forceinline__ V2<C> v2(C a, C b) {
+  V2<C> r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+// component l of an interleaved pair (l is a compile-time constant after unrolling)
+template <class V> __device__ __forceinline__ auto comp(const V& v, int l) -> decltype(v.x) { return l ? v.y : v.x; }
+template <class C> __device__ __forceinline__ V2<C> splat(C a) { return v2<C>(a, a); }
+template <class V> __device__ __forceinline__ V swap_lanes(const V& v) {
+  V r;
+  r.x = v.y;
+  r.y = v.x;
+  return r;
+}
+
+// Lane-wise arithmetic on pairs: one packed FP32x2 instruction in FP32, one instruction per lane in
+// FP64.  Each operation rounds once to nearest, so every lane holds exactly the result of the scalar
+// operation (a - b is the fused b * (-1) + a, exact up to its one rounding).
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 p_add(double2 a, double2 b) {
+  return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 p_mul(double2 a, double2 b) {
+  return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 p_fma(double2 a, double2 b, double2 c) {
+  return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
+}
+template <class V> __device__ __forceinline__ V p_sub(V a, V b) {
+  return p_fma(b, splat<decltype(a.x)>(decltype(a.x)(-1)), a);
+}
+
+template <class C, int TX, int TY, bool NEED_T> struct alignas(16) TileSmem {
   static constexpr int RX = TX + 4, RY = TY + 4;
-  C rho[2][RY][RX];  // density deviations rho_l - rho_bar_l (rho_bar = 0 in FP64)
-  C psi[2][RY][RX];
+  V2<C> rho[RY][RX];  // density deviations rho_l - rho_bar_l (rho_bar = 0 in FP64), components interleaved
+  V2<C> psi[RY][RX];
   C jx[TY][TX], jy[TY][TX];  // bare momentum of the tile's own nodes
   C T[NEED_T ? RY : 1][NEED_T ? RX : 1];
   unsigned char solid[RY][RX];
@@ -192,10 +233,8 @@ template <bool CG> __device__ __forceinline__ float2 ld_pop2(const float2* p) {
 
 template <class C, int TX, int TY, bool NEED_T>
 __device__ __forceinline__ void phase_a_wall(TileSmem<C, TX, TY, NEED_T>& sm, const KParams<C>& kp, int rx, int ry) {
-  sm.rho[0][ry][rx] = kp.drho_w[0];
-  sm.rho[1][ry][rx] = kp.drho_w[1];
-  sm.psi[0][ry][rx] = kp.psi_w[0];
-  sm.psi[1][ry][rx] = kp.psi_w[1];
+  sm.rho[ry][rx] = v2<C>(kp.drho_w[0], kp.drho_w[1]);
+  sm.psi[ry][rx] = v2<C>(kp.psi_w[0], kp.psi_w[1]);
   sm.solid[ry][rx] = 1;
 }
 
@@ -214,15 +253,29 @@ template <class C> __device__ __forceinline__ CompSums<C> comp_sums(const C f[9]
   return r;
 }
 
+// Lane-wise phase-A sums of one component over two nodes (lanes): density deviation and momentum,
+// in the order of comp_sums (bit-identical per lane, up to the sign of an all-zero sum).
+__device__ __forceinline__ void comp_sums2(const float2 u[9], float2& d, float2& jx, float2& jy) {
+  d = u[0];
+#pragma unroll
+  for (int i = 1; i < 9; ++i) d = p_add(d, u[i]);
+  jx = p_add(p_sub(p_sub(p_add(p_sub(u[1], u[3]), u[5]), u[6]), u[7]), u[8]);
+  jy = p_sub(p_sub(p_add(p_add(p_sub(u[2], u[4]), u[5]), u[6]), u[7]), u[8]);
+}
+
+// psi_exp<float> of two values (lanes), with the same roundings.
+__device__ __forceinline__ float2 psi_exp2(float2 rho, float rho0, float inv_rho0) {
+  const float2 x = p_mul(rho, splat<float>(-inv_rho0));
+  return p_fma(splat<float>(-rho0), make_float2(__expf(x.x), __expf(x.y)), splat<float>(rho0));
+}
+
 // The store part of phase_a_node from the component sums (same values, same rounding).
 template <class C, bool SHIFT, int TX, int TY, bool NEED_T>
 __device__ __forceinline__ void phase_a_store(TileSmem<C, TX, TY, NEED_T>& sm, const KParams<C>& kp, int rx, int ry,
                                               const CompSums<C>& a, const CompSums<C>& b) {
   const C rb0 = SHIFT ? kp.rho_bar[0] : C(0), rb1 = SHIFT ? kp.rho_bar[1] : C(0);
-  sm.rho[0][ry][rx] = a.d;
-  sm.rho[1][ry][rx] = b.d;
-  sm.psi[0][ry][rx] = psi_exp<C>(a.d + rb0, kp.rho0, kp.inv_rho0);
-  sm.psi[1][ry][rx] = psi_exp<C>(b.d + rb1, kp.rho0, kp.inv_rho0);
+  sm.rho[ry][rx] = v2<C>(a.d, b.d);
+  sm.psi[ry][rx] = v2<C>(psi_exp<C>(a.d + rb0, kp.rho0, kp.inv_rho0), psi_exp<C>(b.d + rb1, kp.rho0, kp.inv_rho0));
   if (rx >= 2 && rx < TX + 2 && ry >= 2 && ry < TY + 2) {
     sm.jx[ry - 2][rx - 2] = a.jx + b.jx;
     sm.jy[ry - 2][rx - 2] = a.jy + b.jy;
@@ -270,21 +323,29 @@ __device__ __forceinline__ int tile_phase_a_pairs(const SF<S>* __restrict__ fin,
     if (ring_row && ((sa && rx >= 1 && rx <= TX + 2) || (sb && rx + 1 >= 1 && rx + 1 <= TX + 2))) ring_solid = 1;
     CompSums<C> a1{}, a2{}, b1{}, b2{};
     if (!sa && !sb && gxb == gxa + 1 && (gxa & 1) == 0) {
-      // pitch and plane are even, so the pair starts on an 8-byte boundary
+      // pitch and plane are even, so the pair starts on an 8-byte boundary; lanes = (node a, node b)
       const float2* src = reinterpret_cast<const float2*>(fin + (gy * pitch + gxa));
       const int pl2 = plane >> 1;
+      float2 d[2], jx[2], jy[2];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        C fa[9], fb[9];
+        float2 u[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          const float2 u = ld_pop2<CG>(src + (9 * c + i) * pl2);
-          fa[i] = C(u.x);
-          fb[i] = C(u.y);
-        }
-        (c == 0 ? a1 : a2) = comp_sums<C>(fa);
-        (c == 0 ? b1 : b2) = comp_sums<C>(fb);
+        for (int i = 0; i < 9; ++i) u[i] = ld_pop2<CG>(src + (9 * c + i) * pl2);
+        comp_sums2(u, d[c], jx[c], jy[c]);
       }
+      const float2 p1 = psi_exp2(p_add(d[0], splat<float>(kp.rho_bar[0])), kp.rho0, kp.inv_rho0);
+      const float2 p2 = psi_exp2(p_add(d[1], splat<float>(kp.rho_bar[1])), kp.rho0, kp.inv_rho0);
+      // rho[ry][rx .. rx + 1] and psi[ry][rx .. rx + 1] are 16-byte aligned (RX and rx even)
+      *reinterpret_cast<float4*>(&sm.rho[ry][rx]) = make_float4(d[0].x, d[1].x, d[0].y, d[1].y);
+      *reinterpret_cast<float4*>(&sm.psi[ry][rx]) = make_float4(p1.x, p2.x, p1.y, p2.y);
+      sm.solid[ry][rx] = 0;
+      sm.solid[ry][rx + 1] = 0;
+      if (rx >= 2 && rx < TX + 2 && ry >= 2 && ry < TY + 2) {
+        *reinterpret_cast<float2*>(&sm.jx[ry - 2][rx - 2]) = p_add(jx[0], jx[1]);
+        *reinterpret_cast<float2*>(&sm.jy[ry - 2][rx - 2]) = p_add(jy[0], jy[1]);
+      }
+      continue;
     } else {
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
@@ -337,10 +398,8 @@ __device__ __forceinline__ bool tile_phase_a(const SF<S>* __restrict__ fin, cons
     }
     if (solid && rx >= 1 && rx <= TX + 2 && ry >= 1 && ry <= TY + 2) ring_solid = 1;
     if (solid) {
-      sm.rho[0][ry][rx] = kp.drho_w[0];
-      sm.rho[1][ry][rx] = kp.drho_w[1];
-      sm.psi[0][ry][rx] = kp.psi_w[0];
-      sm.psi[1][ry][rx] = kp.psi_w[1];
+      sm.rho[ry][rx] = v2<C>(kp.drho_w[0], kp.drho_w[1]);
+      sm.psi[ry][rx] = v2<C>(kp.psi_w[0], kp.psi_w[1]);
       if constexpr (NEED_T) sm.T[ry][rx] = (2 * gy < ny) ? kp.T_down : kp.T_up;
       sm.solid[ry][rx] = 1;
     } else {
@@ -357,10 +416,8 @@ __device__ __forceinline__ bool tile_phase_a(const SF<S>* __restrict__ fin, cons
         d1 += f[i];
         d2 += h[i];
       }
-      sm.rho[0][ry][rx] = d1;
-      sm.rho[1][ry][rx] = d2;
-      sm.psi[0][ry][rx] = psi_exp<C>(d1 + rb0, kp.rho0, kp.inv_rho0);
-      sm.psi[1][ry][rx] = psi_exp<C>(d2 + rb1, kp.rho0, kp.inv_rho0);
+      sm.rho[ry][rx] = v2<C>(d1, d2);
+      sm.psi[ry][rx] = v2<C>(psi_exp<C>(d1 + rb0, kp.rho0, kp.inv_rho0), psi_exp<C>(d2 + rb1, kp.rho0, kp.inv_rho0));
       if (rx >= 2 && rx < TX + 2 && ry >= 2 && ry < TY + 2) {
         sm.jx[ry - 2][rx - 2] = (f[1] - f[3] + f[5] - f[6] - f[7] + f[8]) + (h[1] - h[3] + h[5] - h[6] - h[7] + h[8]);
         sm.jy[ry - 2][rx - 2] = (f[2] - f[4] + f[5] + f[6] - f[7] - f[8]) + (h[2] - h[4] + h[5] + h[6] - h[7] - h[8]);
@@ -381,55 +438,84 @@ __device__ __forceinline__ bool tile_phase_a(const SF<S>* __restrict__ fin, cons
   return !any && no_wrap_x && no_wrap_y;
 }
 
-// Interaction + external forces at the node whose shared-memory centre is (cx, cy), with the parts
-// the adjoint needs: the cross stencil sum cr = sum_NN w_i rho_m(x + c_i) c_i, the self stencil sum
-// s = sum_24 (G^a w_i + G^r p_i) psi_l(x + c_i) c_i and psi_l(x).
-// SM is any shared-memory view with rho[2][rows][cols] and psi[2][rows][cols] (the tile of the fused
-// step, the row window of the strip-marching step).
+// Interaction force on both fluid components at the node whose shared-memory centre is (cx, cy), lane l
+// for component l: the cross term of Eq. FAB, the attractive and repulsive self terms (Eqs.
+// FintAttrattive, FintRepulsive) and the constant x acceleration.  The buoyancy of Eq. alphaG is left
+// to the caller (buoyant_fy).  Also returns the parts the adjoint needs: cr, the cross stencil sum of
+// the other component's density, sum_NN w_i rho_m(x + c_i) c_i; s, the self stencil sum
+// sum_24 (G^a w_i + G^r p_i) psi_l(x + c_i) c_i, folded as pair differences; and psi_l(x).
+// r = (rho_1, rho_2) at the node.  SM is any shared-memory view with interleaved pairs rho[rows][cols]
+// and psi[rows][cols] (the tile of the fused step, the row window of the strip-marching step).
+template <class C, class SM>
+__device__ __forceinline__ void node_force_pair(const SM& sm, const KParams<C>& kp, int cx, int cy, V2<C> r,
+                                                V2<C>& Fx, V2<C>& Fyp, V2<C>& crx, V2<C>& cry, V2<C>& sx,
+                                                V2<C>& sy, V2<C>& psl) {
+  using V = V2<C>;
+  const auto R = [&](int dy, int dx) -> V { return sm.rho[cy + dy][cx + dx]; };
+  const auto P = [&](int dy, int dx) -> V { return sm.psi[cy + dy][cx + dx]; };
+  // Eq. FAB: -G12/rho0^2 rho_l(x) sum_NN w_i rho_m(x + c_i) c_i; lane m of q holds the sum over rho_m
+  const V e10 = p_sub(R(0, 1), R(0, -1)), e01 = p_sub(R(1, 0), R(-1, 0));
+  const V e11 = p_sub(R(1, 1), R(-1, -1)), em1 = p_sub(R(1, -1), R(-1, 1));
+  const V w1 = splat<C>(C(1) / C(9)), w2 = splat<C>(C(1) / C(36));
+  const V qx = p_fma(w2, p_sub(e11, em1), p_mul(w1, e10));
+  const V qy = p_fma(w2, p_add(e11, em1), p_mul(w1, e01));
+  crx = swap_lanes(qx);  // component l is pushed by the other component's density
+  cry = swap_lanes(qy);
+  // Eqs. FintAttrattive + FintRepulsive: -psi_l(x) sum_24 (G^a w_i + G^r p_i) psi_l(x + c_i) c_i
+  const V d10 = p_sub(P(0, 1), P(0, -1)), d01 = p_sub(P(1, 0), P(-1, 0));
+  const V d11 = p_sub(P(1, 1), P(-1, -1)), dm1 = p_sub(P(1, -1), P(-1, 1));
+  const V d20 = p_sub(P(0, 2), P(0, -2)), d02 = p_sub(P(2, 0), P(-2, 0));
+  const V d12 = p_sub(P(2, 1), P(-2, -1)), dm12 = p_sub(P(2, -1), P(-2, 1));
+  const V d21 = p_sub(P(1, 2), P(-1, -2)), dm21 = p_sub(P(1, -2), P(-1, 2));
+  const V d22 = p_sub(P(2, 2), P(-2, -2)), dm22 = p_sub(P(2, -2), P(-2, 2));
+  const V a1 = v2<C>(kp.a1[0], kp.a1[1]), a2 = v2<C>(kp.a2[0], kp.a2[1]);
+  const V a4 = v2<C>(kp.a4x2[0], kp.a4x2[1]), a5 = v2<C>(kp.a5[0], kp.a5[1]);
+  const V a8 = v2<C>(kp.a8x2[0], kp.a8x2[1]), two = splat<C>(C(2));
+  // x: a1 d10 + a2 (d11 - dm1) + 2 a4 d20 + a5 (d12 - dm12 + 2 (d21 - dm21)) + 2 a8 (d22 - dm22)
+  V t = p_mul(a1, d10);
+  t = p_fma(a2, p_sub(d11, dm1), t);
+  t = p_fma(a4, d20, t);
+  t = p_fma(a5, p_fma(two, p_sub(d21, dm21), p_sub(d12, dm12)), t);
+  sx = p_fma(a8, p_sub(d22, dm22), t);
+  // y: a1 d01 + a2 (d11 + dm1) + 2 a4 d02 + a5 (2 (d12 + dm12) + d21 + dm21) + 2 a8 (d22 + dm22)
+  t = p_mul(a1, d01);
+  t = p_fma(a2, p_add(d11, dm1), t);
+  t = p_fma(a4, d02, t);
+  t = p_fma(a5, p_fma(two, p_add(d12, dm12), p_add(d21, dm21)), t);
+  sy = p_fma(a8, p_add(d22, dm22), t);
+  psl = P(0, 0);
+  const V npsl = p_mul(psl, splat<C>(C(-1)));
+  const V gr = p_mul(splat<C>(-kp.gx), r);
+  Fx = p_fma(r, splat<C>(kp.body_fx), p_fma(npsl, sx, p_mul(gr, crx)));
+  Fyp = p_fma(npsl, sy, p_mul(gr, cry));
+}
+
+// Fy of both components: the interaction part plus the buoyancy rho_l alpha_g T of Eq. alphaG.
+template <class C> __device__ __forceinline__ V2<C> buoyant_fy(const KParams<C>& kp, V2<C> Fyp, V2<C> r, C T) {
+  return p_fma(p_mul(r, splat<C>(kp.alpha_g)), splat<C>(T), Fyp);
+}
+
+// Forces with their adjoint parts per component (arrays indexed by component).
 template <class C, class SM>
 __device__ __forceinline__ void node_force_parts(const SM& sm, const KParams<C>& kp, int cx, int cy, C r1, C r2, C T,
                                                  C Fx[2], C Fy[2], C crx[2], C cry[2], C sx[2], C sy[2], C psl[2]) {
-#pragma unroll
-  for (int l = 0; l < 2; ++l) {
-    const int m = 1 - l;
-    // Eq. FAB on rho: -G12/rho0^2 rho_l(x) sum_{NN} w_i rho_m(x + c_i) c_i, as pair differences
-    const C e10 = sm.rho[m][cy][cx + 1] - sm.rho[m][cy][cx - 1];
-    const C e01 = sm.rho[m][cy + 1][cx] - sm.rho[m][cy - 1][cx];
-    const C e11 = sm.rho[m][cy + 1][cx + 1] - sm.rho[m][cy - 1][cx - 1];
-    const C em1 = sm.rho[m][cy + 1][cx - 1] - sm.rho[m][cy - 1][cx + 1];
-    const C w1 = C(1) / C(9), w2 = C(1) / C(36);
-    crx[l] = w1 * e10 + w2 * (e11 - em1);
-    cry[l] = w1 * e01 + w2 * (e11 + em1);
-    const C rl = (l == 0) ? r1 : r2;
-    // Eqs. FintAttrattive + FintRepulsive: -psi_l(x) sum_{24 links} (G^a w_i + G^r p_i) psi_l(x + c_i) c_i
-    const C d10 = sm.psi[l][cy][cx + 1] - sm.psi[l][cy][cx - 1];
-    const C d01 = sm.psi[l][cy + 1][cx] - sm.psi[l][cy - 1][cx];
-    const C d11 = sm.psi[l][cy + 1][cx + 1] - sm.psi[l][cy - 1][cx - 1];
-    const C dm1 = sm.psi[l][cy + 1][cx - 1] - sm.psi[l][cy - 1][cx + 1];
-    const C d20 = sm.psi[l][cy][cx + 2] - sm.psi[l][cy][cx - 2];
-    const C d02 = sm.psi[l][cy + 2][cx] - sm.psi[l][cy - 2][cx];
-    const C d12 = sm.psi[l][cy + 2][cx + 1] - sm.psi[l][cy - 2][cx - 1];
-    const C dm12 = sm.psi[l][cy + 2][cx - 1] - sm.psi[l][cy - 2][cx + 1];
-    const C d21 = sm.psi[l][cy + 1][cx + 2] - sm.psi[l][cy - 1][cx - 2];
-    const C dm21 = sm.psi[l][cy + 1][cx - 2] - sm.psi[l][cy - 1][cx + 2];
-    const C d22 = sm.psi[l][cy + 2][cx + 2] - sm.psi[l][cy - 2][cx - 2];
-    const C dm22 = sm.psi[l][cy + 2][cx - 2] - sm.psi[l][cy - 2][cx + 2];
-    sx[l] = kp.a1[l] * d10 + kp.a2[l] * (d11 - dm1) + kp.a4x2[l] * d20 +
-            kp.a5[l] * (d12 - dm12 + C(2) * (d21 - dm21)) + kp.a8x2[l] * (d22 - dm22);
-    sy[l] = kp.a1[l] * d01 + kp.a2[l] * (d11 + dm1) + kp.a4x2[l] * d02 +
-            kp.a5[l] * (C(2) * (d12 + dm12) + d21 + dm21) + kp.a8x2[l] * (d22 + dm22);
-    psl[l] = sm.psi[l][cy][cx];
-    // Eq. alphaG (and the constant x acceleration)
-    Fx[l] = -kp.gx * rl * crx[l] - psl[l] * sx[l] + rl * kp.body_fx;
-    Fy[l] = -kp.gx * rl * cry[l] - psl[l] * sy[l] + rl * kp.alpha_g * T;
-  }
+  V2<C> fx, fyp, qx, qy, tx, ty, ps;
+  const V2<C> r = v2<C>(r1, r2);
+  node_force_pair<C, SM>(sm, kp, cx, cy, r, fx, fyp, qx, qy, tx, ty, ps);
+  const V2<C> fy = buoyant_fy<C>(kp, fyp, r, T);
+  Fx[0] = fx.x, Fx[1] = fx.y, Fy[0] = fy.x, Fy[1] = fy.y;
+  crx[0] = qx.x, crx[1] = qx.y, cry[0] = qy.x, cry[1] = qy.y;
+  sx[0] = tx.x, sx[1] = tx.y, sy[0] = ty.x, sy[1] = ty.y, psl[0] = ps.x, psl[1] = ps.y;
 }
 
 template <class C, class SM>
 __device__ __forceinline__ void node_forces(const SM& sm, const KParams<C>& kp, int cx, int cy, C r1, C r2, C T,
                                             C Fx[2], C Fy[2]) {
-  C crx[2], cry[2], sx[2], sy[2], psl[2];
-  node_force_parts<C, SM>(sm, kp, cx, cy, r1, r2, T, Fx, Fy, crx, cry, sx, sy, psl);
+  V2<C> fx, fyp, qx, qy, tx, ty, ps;
+  const V2<C> r = v2<C>(r1, r2);
+  node_force_pair<C, SM>(sm, kp, cx, cy, r, fx, fyp, qx, qy, tx, ty, ps);
+  const V2<C> fy = buoyant_fy<C>(kp, fyp, r, T);
+  Fx[0] = fx.x, Fx[1] = fx.y, Fy[0] = fy.x, Fy[1] = fy.y;
 }
 
 // Reciprocals of rho_1, rho_2 and rho_1 + rho_2 from one division.
@@ -443,41 +529,71 @@ template <class C> __device__ __forceinline__ void three_reciprocals(C r1, C r2,
 }
 
 // BGK relaxation of the 27 populations of one node (Eqs. BGK, LBMg, Teq); in shifted storage the
-// deviations relax: f^eq - w_i rho_bar = w_i (drho + rho P_i(u)).  With tau = 1 (tau_g = 1) the
-// post-collision population is the equilibrium itself and the relaxation arithmetic is skipped.
+// deviations relax: f^eq - w_i rho_bar = w_i (drho + rho P_i(u)) with P_i(u) = 3 c_i.u + 4.5 (c_i.u)^2
+// - 1.5 u^2.  With tau = 1 (tau_g = 1) the post-collision population is the equilibrium itself and the
+// relaxation arithmetic is skipped.  The fluid components are computed as lane pairs; for the
+// direction opposite to c_i, P = c_i.u (4.5 c_i.u - 3) - 1.5 u^2, which is P at -c_i.u exactly.
 template <class C, bool SHIFT, bool RELAX>
 __device__ __forceinline__ void collide_fluid(const KParams<C>& kp, const C f[9], const C h[9], C r1, C r2, C dr1,
                                               C dr2, C ux, C uy, C irl0, C irl1, const C Fx[2], const C Fy[2],
                                               C post[27]) {
+  using V = V2<C>;
+  const V r = v2<C>(r1, r2), ir = v2<C>(irl0, irl1);
+  const V tau = splat<C>(kp.tau);
+  // Eq. shift: u_l = u + tau F_l / rho_l
+  const V ulx = p_fma(p_mul(tau, v2<C>(Fx[0], Fx[1])), ir, splat<C>(ux));
+  const V uly = p_fma(p_mul(tau, v2<C>(Fy[0], Fy[1])), ir, splat<C>(uy));
+  const V nusq = p_mul(splat<C>(C(-1.5)), p_fma(ulx, ulx, p_mul(uly, uly)));
+  const V base = SHIFT ? v2<C>(dr1, dr2) : r;
+  const V k45 = splat<C>(C(4.5)), p3 = splat<C>(C(3)), m3 = splat<C>(C(-3));
+  V cu[9];
+  cu[1] = ulx, cu[2] = uly, cu[5] = p_add(ulx, uly), cu[6] = p_sub(uly, ulx);
+  V feq[9];
+  feq[0] = p_mul(splat<C>(wq<C>(0)), p_fma(r, nusq, base));
 #pragma unroll
-  for (int l = 0; l < 2; ++l) {
-    const C rl = (l == 0) ? r1 : r2;
-    const C inv_rl = (l == 0) ? irl0 : irl1;
-    const C ulx = ux + kp.tau * Fx[l] * inv_rl, uly = uy + kp.tau * Fy[l] * inv_rl;
-    const C usq = C(1.5) * (ulx * ulx + uly * uly);
-    const C base = SHIFT ? ((l == 0) ? dr1 : dr2) : rl;
-    const C* pop = (l == 0) ? f : h;
+  for (int i = 1; i < 9; ++i) {
+    const bool odd = (i == 3 || i == 4 || i == 7 || i == 8);
+    const V c = cu[odd ? oppq(i) : i];
+    const V poly = p_fma(c, p_fma(k45, c, odd ? m3 : p3), nusq);
+    feq[i] = p_mul(splat<C>(wq<C>(i)), p_fma(r, poly, base));
+  }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const C cu = C(cxq(i)) * ulx + C(cyq(i)) * uly;
-      const C poly = cu * (C(3) + C(4.5) * cu) - usq;
-      const C feq = wq<C>(i) * (base + rl * poly);
-      post[9 * l + i] = RELAX ? pop[i] + (feq - pop[i]) * kp.inv_tau : feq;
+  for (int i = 0; i < 9; ++i) {
+    V q = feq[i];
+    if constexpr (RELAX) {
+      const V pop = v2<C>(f[i], h[i]);
+      q = p_fma(p_sub(q, pop), splat<C>(kp.inv_tau), pop);
     }
+    post[i] = q.x;
+    post[9 + i] = q.y;
   }
 }
 
+// Thermal equilibria (Eq. Teq) with u^(H), the directions paired with their opposites as lanes.
 template <class C, bool SHIFT, bool RELAX>
 __device__ __forceinline__ void collide_thermal(const KParams<C>& kp, const C g[9], C T, C dT, C uHx, C uHy,
                                                 C post[27]) {
-  const C usq = C(1.5) * (uHx * uHx + uHy * uHy);
+  using V = V2<C>;
+  const C nusq = C(-1.5) * (uHx * uHx + uHy * uHy);
   const C base = SHIFT ? dT : T;
+  const V vn = splat<C>(nusq), vT = splat<C>(T), vb = splat<C>(base), k45 = splat<C>(C(4.5));
+  const V pm3 = v2<C>(C(3), C(-3));
+  const C g0 = wq<C>(0) * (base + T * nusq);
+  post[18] = RELAX ? g[0] + (g0 - g[0]) * kp.inv_tau_g : g0;
+  const C cus[4] = {uHx, uHy, uHx + uHy, uHy - uHx};
+  const int dir[4] = {1, 2, 5, 6};
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const C cu = C(cxq(i)) * uHx + C(cyq(i)) * uHy;
-    const C poly = cu * (C(3) + C(4.5) * cu) - usq;
-    const C geq = wq<C>(i) * (base + T * poly);
-    post[18 + i] = RELAX ? g[i] + (geq - g[i]) * kp.inv_tau_g : geq;
+  for (int k = 0; k < 4; ++k) {
+    const int i = dir[k], o = oppq(i);
+    const V c = splat<C>(cus[k]);
+    const V poly = p_fma(c, p_fma(k45, c, pm3), vn);
+    V q = p_mul(splat<C>(wq<C>(i)), p_fma(vT, poly, vb));
+    if constexpr (RELAX) {
+      const V pop = v2<C>(g[i], g[o]);
+      q = p_fma(p_sub(q, pop), splat<C>(kp.inv_tau_g), pop);
+    }
+    post[18 + i] = q.x;
+    post[18 + o] = q.y;
   }
 }
 
@@ -587,7 +703,7 @@ __device__ __forceinline__ void tile_phase_b(const Src& pop, SF<S>* __restrict__
         h[i] = C(pop(9 + i, idx, tx, ty));
       }
     }
-    const C dr1 = sm.rho[0][cy][cx], dr2 = sm.rho[1][cy][cx];
+    const C dr1 = sm.rho[cy][cx].x, dr2 = sm.rho[cy][cx].y;
     const C r1 = SHIFT ? dr1 + kp.rho_bar[0] : dr1, r2 = SHIFT ? dr2 + kp.rho_bar[1] : dr2;
     C dT = C(0);
 #pragma unroll

@@ -41,8 +41,8 @@ constexpr int kSWR = 3 * kSR;    // window rows: groups of parity 0, 1, then par
 constexpr int kSNT = kSW * kSR;  // threads per CTA: one node of a group each
 
 struct StreamWin {
-  float rho[2][kSWR][kSRX];  // density deviations rho_l - rho_bar_l
-  float psi[2][kSWR][kSRX];
+  float2 rho[kSWR][kSRX];  // density deviations rho_l - rho_bar_l, components interleaved
+  float2 psi[kSWR][kSRX];
   float jx[kSWR][kSW], jy[kSWR][kSW];
   unsigned char solid[kSWR][kSRX];
 };
@@ -68,7 +68,7 @@ __device__ __forceinline__ void stream_node(const float* __restrict__ fin, float
       h[i] = fin[idx + (9 + i) * plane];
     }
   }
-  const float dr1 = w.rho[0][cy][cx], dr2 = w.rho[1][cy][cx];
+  const float dr1 = w.rho[cy][cx].x, dr2 = w.rho[cy][cx].y;
   const float r1 = dr1 + kp.rho_bar[0], r2 = dr2 + kp.rho_bar[1];
   float dT = 0.0f;
 #pragma unroll
@@ -201,16 +201,12 @@ lb_step_stream_kernel(const __grid_constant__ CUtensorMap map_fluid, const float
           }
         }
       }
-      sm.w.rho[0][wr][rx] = d1;
-      sm.w.rho[1][wr][rx] = d2;
-      sm.w.psi[0][wr][rx] = p1;
-      sm.w.psi[1][wr][rx] = p2;
+      sm.w.rho[wr][rx] = make_float2(d1, d2);
+      sm.w.psi[wr][rx] = make_float2(p1, p2);
       sm.w.solid[wr][rx] = solid ? 1 : 0;
       if (mirror) {
-        sm.w.rho[0][wr + 2 * kSR][rx] = d1;
-        sm.w.rho[1][wr + 2 * kSR][rx] = d2;
-        sm.w.psi[0][wr + 2 * kSR][rx] = p1;
-        sm.w.psi[1][wr + 2 * kSR][rx] = p2;
+        sm.w.rho[wr + 2 * kSR][rx] = make_float2(d1, d2);
+        sm.w.psi[wr + 2 * kSR][rx] = make_float2(p1, p2);
         sm.w.solid[wr + 2 * kSR][rx] = solid ? 1 : 0;
       }
     }

@@ -64,10 +64,8 @@ __device__ __forceinline__ bool tma_phase_a(const float* __restrict__ fin, const
     }
     if (solid && rx >= 1 && rx <= TX + 2 && ry >= 1 && ry <= TY + 2) ring_solid = 1;
     if (solid) {
-      sm.rho[0][ry][rx] = kp.drho_w[0];
-      sm.rho[1][ry][rx] = kp.drho_w[1];
-      sm.psi[0][ry][rx] = kp.psi_w[0];
-      sm.psi[1][ry][rx] = kp.psi_w[1];
+      sm.rho[ry][rx] = v2<float>(kp.drho_w[0], kp.drho_w[1]);
+      sm.psi[ry][rx] = v2<float>(kp.psi_w[0], kp.psi_w[1]);
       sm.solid[ry][rx] = 1;
       continue;
     }
@@ -93,10 +91,9 @@ __device__ __forceinline__ bool tma_phase_a(const float* __restrict__ fin, const
       d1 += f[i];
       d2 += h[i];
     }
-    sm.rho[0][ry][rx] = d1;
-    sm.rho[1][ry][rx] = d2;
-    sm.psi[0][ry][rx] = psi_exp<float>(d1 + kp.rho_bar[0], kp.rho0, kp.inv_rho0);
-    sm.psi[1][ry][rx] = psi_exp<float>(d2 + kp.rho_bar[1], kp.rho0, kp.inv_rho0);
+    sm.rho[ry][rx] = v2<float>(d1, d2);
+    sm.psi[ry][rx] = v2<float>(psi_exp<float>(d1 + kp.rho_bar[0], kp.rho0, kp.inv_rho0),
+                               psi_exp<float>(d2 + kp.rho_bar[1], kp.rho0, kp.inv_rho0));
     if (rx >= 2 && rx < TX + 2 && ry >= 2 && ry < TY + 2) {
       sm.jx[ry - 2][rx - 2] = (f[1] - f[3] + f[5] - f[6] - f[7] + f[8]) + (h[1] - h[3] + h[5] - h[6] - h[7] + h[8]);
       sm.jy[ry - 2][rx - 2] = (f[2] - f[4] + f[5] + f[6] - f[7] - f[8]) + (h[2] - h[4] + h[5] + h[6] - h[7] - h[8]);
