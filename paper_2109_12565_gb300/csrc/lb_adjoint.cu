@@ -13,7 +13,8 @@
 //         u^(H), u = j / rho and the buoyancy, and the parts of the force
 //         adjoint local to the node; it writes lam_t minus the non-local
 //         density terms, plus lam_F (the adjoint of the four force
-//         components) and accumulates dJ/dT_down per block;
+//         components) and the node densities, and accumulates dJ/dT_down
+//         per block;
 //   adj2  gathers lam_F over the transposed stencils (8 links for the cross
 //         force, 24 for the self force) on a 2-node ring, maps the
 //         pseudo-potential adjoints back to the densities and adds them to
@@ -41,7 +42,7 @@ namespace tlb {
 // registers without spills at 3 CTAs per SM; FP64 needs its ~240 registers (a cap spills).
 template <class S> struct AdjTile;
 template <> struct AdjTile<double> { static constexpr int TX = 32, TY = 16, BY = 8, MINB = 1; };
-template <> struct AdjTile<float> { static constexpr int TX = 32, TY = 16, BY = 8, MINB = 3; };
+template <> struct AdjTile<float> { static constexpr int TX = 32, TY = 8, BY = 8, MINB = 3; };
 
 template <class S, class C, bool SHIFT, int TX, int TY, int BY, int MINB>
 __global__ void __launch_bounds__(TX * BY, MINB)
@@ -69,7 +70,7 @@ lb_adj1_kernel(const S* __restrict__ fin, const S* __restrict__ lam_out, S* __re
 #pragma unroll
       for (int q = 0; q < 27; ++q) lam_in[q * plane + idx] = S(0);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) lamF[q * plane + idx] = S(0);
+      for (int q = 0; q < 6; ++q) lamF[q * plane + idx] = S(0);
       continue;
     }
     // ---- forward quantities of S_t at the node
@@ -80,6 +81,8 @@ lb_adj1_kernel(const S* __restrict__ fin, const S* __restrict__ lam_out, S* __re
     const C r1 = sm.rho[cy][cx].x + (SHIFT ? kp.rho_bar[0] : C(0));
     const C r2 = sm.rho[cy][cx].y + (SHIFT ? kp.rho_bar[1] : C(0));
     const C jx = sm.jx[ty][tx], jy = sm.jy[ty][tx];
+    lamF[4 * plane + idx] = S(r1);  // the densities, for adj2's transposed stencils
+    lamF[5 * plane + idx] = S(r2);
     C Fx[2], Fy[2], crx[2], cry[2], sx[2], sy[2], psl[2];
     node_force_parts<C>(sm, kp, cx, cy, r1, r2, T, Fx, Fy, crx, cry, sx, sy, psl);
     const C rho = r1 + r2;
@@ -226,14 +229,22 @@ template <class C, int TX, int TY> struct Adj2Smem {
 
 template <class S, class C, bool SHIFT, int TX, int TY, int BY, int MINB>
 __global__ void __launch_bounds__(TX * BY, MINB)
-lb_adj2_kernel(const S* __restrict__ fin, const S* __restrict__ lamF, S* __restrict__ lam_in, const KParams<C> kp) {
+lb_adj2_kernel(const S* __restrict__ lamF, S* __restrict__ lam_in, const KParams<C> kp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto& sm = *reinterpret_cast<Adj2Smem<C, TX, TY>*>(smem_raw);
   constexpr int RX = TX + 4, RY = TY + 4, NT = TX * BY;
   const int tid = threadIdx.y * TX + threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int nx = kp.nx, ny = kp.ny, pitch = kp.pitch, plane = kp.plane;
-  for (int r = tid; r < RX * RY; r += NT) {
+  // Ring positions of this thread: all their loads are issued before any of them is used.
+  constexpr int NR = (RX * RY + NT - 1) / NT;
+  C val[NR][6];
+  bool fluid[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    const int r = tid + q * NT;
+    fluid[q] = false;
+    if (r >= RX * RY) continue;
     const int ry = r / RX, rx = r - ry * RX;
     const int gx = wrap_any(x0 + rx - 2, nx);
     int gy = y0 + ry - 2;
@@ -244,8 +255,20 @@ lb_adj2_kernel(const S* __restrict__ fin, const S* __restrict__ lamF, S* __restr
     } else {
       solid = (gy <= 0 || gy >= ny - 1) || (kp.mask != nullptr && kp.mask[gy * nx + gx] != 0);
     }
+    if (solid) continue;
+    fluid[q] = true;
+    const int idx = gy * pitch + gx;
+    // lam_F (x, y) of both components, then the densities written by adj1
+#pragma unroll
+    for (int v = 0; v < 6; ++v) val[q][v] = C(lamF[v * plane + idx]);
+  }
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    const int r = tid + q * NT;
+    if (r >= RX * RY) continue;
+    const int ry = r / RX, rx = r - ry * RX;
     const bool own = rx >= 2 && rx < TX + 2 && ry >= 2 && ry < TY + 2;
-    if (solid) {
+    if (!fluid[q]) {
 #pragma unroll
       for (int l = 0; l < 2; ++l)
 #pragma unroll
@@ -253,18 +276,11 @@ lb_adj2_kernel(const S* __restrict__ fin, const S* __restrict__ lamF, S* __restr
       if (own) sm.solid[ry - 2][rx - 2] = 1;
       continue;
     }
-    const int idx = gy * pitch + gx;
-    C d1 = C(0), d2 = C(0);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      d1 += C(fin[i * plane + idx]);
-      d2 += C(fin[(9 + i) * plane + idx]);
-    }
-    const C rr[2] = {d1 + (SHIFT ? kp.rho_bar[0] : C(0)), d2 + (SHIFT ? kp.rho_bar[1] : C(0))};
+    const C rr[2] = {val[q][4], val[q][5]};
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
       const C ps = psi_exp<C>(rr[l], kp.rho0, kp.inv_rho0);
-      const C fx = C(lamF[(2 * l) * plane + idx]), fy = C(lamF[(2 * l + 1) * plane + idx]);
+      const C fx = val[q][2 * l], fy = val[q][2 * l + 1];
       sm.vt[l][0][ry][rx] = rr[l] * fx;
       sm.vt[l][1][ry][rx] = rr[l] * fy;
       sm.ve[l][0][ry][rx] = ps * fx;
@@ -306,13 +322,13 @@ lb_adj2_kernel(const S* __restrict__ fin, const S* __restrict__ lamF, S* __restr
 #undef TLB_DX
 #undef TLB_DY
     const int idx = gy * pitch + gx;
+    // all 18 loads before the stores: through one pointer with a run-time plane stride the compiler
+    // cannot tell the entries apart, and a load after a store would wait for it
+    C v[18];
 #pragma unroll
-    for (int l = 0; l < 2; ++l)
+    for (int q = 0; q < 18; ++q) v[q] = C(lam_in[q * plane + idx]);
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        S* p = lam_in + (9 * l + i) * plane + idx;
-        *p = S(C(*p) + lrho[l]);
-      }
+    for (int q = 0; q < 18; ++q) lam_in[q * plane + idx] = S(v[q] + lrho[q / 9]);
   }
 }
 
@@ -376,7 +392,7 @@ cudaError_t adj_step_impl(const StepCfg& c, const void* S_t, const void* lam_out
                              static_cast<S*>(lamF), kp, S(cJ), S(nuc), mirror_coef, acc);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k2<<<grid, block, b2, s>>>(static_cast<const S*>(S_t), static_cast<const S*>(lamF), static_cast<S*>(lam_in), kp);
+  k2<<<grid, block, b2, s>>>(static_cast<const S*>(lamF), static_cast<S*>(lam_in), kp);
   return cudaGetLastError();
 }
 
@@ -406,7 +422,7 @@ AdjLayout adj_layout(const lb_handle* h, int n_steps, int ckpt_every) {
   A.lam = off;
   off += 2 * st;
   A.lamF = off;
-  off += round_up(4 * plane * h->L.elem, kAlign);
+  off += round_up(6 * plane * h->L.elem, kAlign);
   A.acc = off;
   off += round_up((size_t)A.n_blocks * sizeof(double), kAlign);
   A.red = off;
