@@ -215,6 +215,14 @@ __device__ __forceinline__ double2 p_fma(double2 a, double2 b, double2 c) {
 template <class V> __device__ __forceinline__ V p_sub(V a, V b) {
   return p_fma(b, splat<decltype(a.x)>(decltype(a.x)(-1)), a);
 }
+// Scalar operations with one rounding each, never fused beyond what is written, so that every caller
+// of the functions below computes the same bits.
+__device__ __forceinline__ float s_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float s_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float s_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double s_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double s_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double s_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 template <class C, int TX, int TY, bool NEED_T> struct alignas(16) TileSmem {
   static constexpr int RX = TX + 4, RY = TY + 4;
@@ -438,56 +446,110 @@ __device__ __forceinline__ bool tile_phase_a(const SF<S>* __restrict__ fin, cons
   return !any && no_wrap_x && no_wrap_y;
 }
 
+// Stencil sums of one node, accumulated row pair by row pair (row 0, rows +-1, rows +-2), which keeps
+// only two stencil rows live at a time.  Lane l holds component l (for q,
+// the density of component l).  q: Eq. FAB's cross sums sum_NN w_i rho(x + c_i) c_i; s: the self
+// sums sum_24 (G^a w_i + G^r p_i) psi_l(x + c_i) c_i of Eqs. FintAttrattive + FintRepulsive, folded
+// as pair differences; u5x, v5y: the rows +-1 parts of the (2, 1)-link terms, finished with rows +-2.
+template <class C> struct StencilSums {
+  V2<C> qx, qy, sx, sy, u5x, v5y;
+};
+
+// Row 0: p[k] = psi(x + (k - 2, 0)), rm / rp = rho(x -+ (1, 0)).
+template <class C>
+__device__ __forceinline__ void sums_row0(StencilSums<C>& a, const KParams<C>& kp, const V2<C> p[5], V2<C> rm,
+                                          V2<C> rp) {
+  a.qx = p_mul(splat<C>(C(1) / C(9)), p_sub(rp, rm));
+  a.sx = p_fma(v2<C>(kp.a4x2[0], kp.a4x2[1]), p_sub(p[4], p[0]),
+               p_mul(v2<C>(kp.a1[0], kp.a1[1]), p_sub(p[3], p[1])));
+}
+
+// Rows +-1: pu[k] = psi(x + (k - 2, 1)), pd[k] = psi(x + (k - 2, -1)), ru[k] = rho(x + (k - 1, 1)),
+// rd[k] = rho(x + (k - 1, -1)).
+template <class C>
+__device__ __forceinline__ void sums_row1(StencilSums<C>& a, const KParams<C>& kp, const V2<C> pu[5],
+                                          const V2<C> pd[5], const V2<C> ru[3], const V2<C> rd[3]) {
+  using V = V2<C>;
+  const V w1 = splat<C>(C(1) / C(9)), w2 = splat<C>(C(1) / C(36));
+  const V e01 = p_sub(ru[1], rd[1]), e11 = p_sub(ru[2], rd[0]), em1 = p_sub(ru[0], rd[2]);
+  a.qx = p_fma(w2, p_sub(e11, em1), a.qx);
+  a.qy = p_fma(w2, p_add(e11, em1), p_mul(w1, e01));
+  const V d01 = p_sub(pu[2], pd[2]), d11 = p_sub(pu[3], pd[1]), dm1 = p_sub(pu[1], pd[3]);
+  const V d21 = p_sub(pu[4], pd[0]), dm21 = p_sub(pu[0], pd[4]);
+  const V a2 = v2<C>(kp.a2[0], kp.a2[1]);
+  a.sx = p_fma(a2, p_sub(d11, dm1), a.sx);
+  a.sy = p_fma(a2, p_add(d11, dm1), p_mul(v2<C>(kp.a1[0], kp.a1[1]), d01));
+  a.u5x = p_sub(d21, dm21);
+  a.v5y = p_add(d21, dm21);
+}
+
+// Rows +-2: pu[k] = psi(x + (k - 2, 2)), pd[k] = psi(x + (k - 2, -2)).
+template <class C>
+__device__ __forceinline__ void sums_row2(StencilSums<C>& a, const KParams<C>& kp, const V2<C> pu[5],
+                                          const V2<C> pd[5]) {
+  using V = V2<C>;
+  const V two = splat<C>(C(2));
+  const V a5 = v2<C>(kp.a5[0], kp.a5[1]), a8 = v2<C>(kp.a8x2[0], kp.a8x2[1]);
+  const V d02 = p_sub(pu[2], pd[2]), d12 = p_sub(pu[3], pd[1]), dm12 = p_sub(pu[1], pd[3]);
+  const V d22 = p_sub(pu[4], pd[0]), dm22 = p_sub(pu[0], pd[4]);
+  a.sx = p_fma(a5, p_fma(two, a.u5x, p_sub(d12, dm12)), a.sx);
+  a.sx = p_fma(a8, p_sub(d22, dm22), a.sx);
+  a.sy = p_fma(v2<C>(kp.a4x2[0], kp.a4x2[1]), d02, a.sy);
+  a.sy = p_fma(a5, p_fma(two, p_add(d12, dm12), a.v5y), a.sy);
+  a.sy = p_fma(a8, p_add(d22, dm22), a.sy);
+}
+
+// Forces from the stencil sums: lane l for component l, the constant x acceleration included, the
+// buoyancy of Eq. alphaG left to the caller (buoyant_fy).  crx / cry: the cross sums of the other
+// component's density; psl = psi(x); r = (rho_1, rho_2) at the node.
+template <class C>
+__device__ __forceinline__ void sums_forces(const StencilSums<C>& a, const KParams<C>& kp, V2<C> r, V2<C> psl,
+                                            V2<C>& Fx, V2<C>& Fyp, V2<C>& crx, V2<C>& cry) {
+  using V = V2<C>;
+  crx = swap_lanes(a.qx);  // component l is pushed by the other component's density
+  cry = swap_lanes(a.qy);
+  const V npsl = p_mul(psl, splat<C>(C(-1)));
+  const V gr = p_mul(splat<C>(-kp.gx), r);
+  Fx = p_fma(r, splat<C>(kp.body_fx), p_fma(npsl, a.sx, p_mul(gr, crx)));
+  Fyp = p_fma(npsl, a.sy, p_mul(gr, cry));
+}
+
 // Interaction force on both fluid components at the node whose shared-memory centre is (cx, cy), lane l
-// for component l: the cross term of Eq. FAB, the attractive and repulsive self terms (Eqs.
-// FintAttrattive, FintRepulsive) and the constant x acceleration.  The buoyancy of Eq. alphaG is left
-// to the caller (buoyant_fy).  Also returns the parts the adjoint needs: cr, the cross stencil sum of
-// the other component's density, sum_NN w_i rho_m(x + c_i) c_i; s, the self stencil sum
-// sum_24 (G^a w_i + G^r p_i) psi_l(x + c_i) c_i, folded as pair differences; and psi_l(x).
-// r = (rho_1, rho_2) at the node.  SM is any shared-memory view with interleaved pairs rho[rows][cols]
-// and psi[rows][cols] (the tile of the fused step, the row window of the strip-marching step).
+// for component l (Eqs. FAB, FintAttrattive, FintRepulsive, with the constant x acceleration; the
+// buoyancy is left to the caller), and the parts the adjoint needs: cr, s and psi_l(x) (see
+// StencilSums).  SM is any shared-memory view with interleaved pairs rho[rows][cols] and
+// psi[rows][cols] (the tile of the fused step, the row window of the strip-marching step).
 template <class C, class SM>
 __device__ __forceinline__ void node_force_pair(const SM& sm, const KParams<C>& kp, int cx, int cy, V2<C> r,
                                                 V2<C>& Fx, V2<C>& Fyp, V2<C>& crx, V2<C>& cry, V2<C>& sx,
                                                 V2<C>& sy, V2<C>& psl) {
   using V = V2<C>;
-  const auto R = [&](int dy, int dx) -> V { return sm.rho[cy + dy][cx + dx]; };
-  const auto P = [&](int dy, int dx) -> V { return sm.psi[cy + dy][cx + dx]; };
-  // Eq. FAB: -G12/rho0^2 rho_l(x) sum_NN w_i rho_m(x + c_i) c_i; lane m of q holds the sum over rho_m
-  const V e10 = p_sub(R(0, 1), R(0, -1)), e01 = p_sub(R(1, 0), R(-1, 0));
-  const V e11 = p_sub(R(1, 1), R(-1, -1)), em1 = p_sub(R(1, -1), R(-1, 1));
-  const V w1 = splat<C>(C(1) / C(9)), w2 = splat<C>(C(1) / C(36));
-  const V qx = p_fma(w2, p_sub(e11, em1), p_mul(w1, e10));
-  const V qy = p_fma(w2, p_add(e11, em1), p_mul(w1, e01));
-  crx = swap_lanes(qx);  // component l is pushed by the other component's density
-  cry = swap_lanes(qy);
-  // Eqs. FintAttrattive + FintRepulsive: -psi_l(x) sum_24 (G^a w_i + G^r p_i) psi_l(x + c_i) c_i
-  const V d10 = p_sub(P(0, 1), P(0, -1)), d01 = p_sub(P(1, 0), P(-1, 0));
-  const V d11 = p_sub(P(1, 1), P(-1, -1)), dm1 = p_sub(P(1, -1), P(-1, 1));
-  const V d20 = p_sub(P(0, 2), P(0, -2)), d02 = p_sub(P(2, 0), P(-2, 0));
-  const V d12 = p_sub(P(2, 1), P(-2, -1)), dm12 = p_sub(P(2, -1), P(-2, 1));
-  const V d21 = p_sub(P(1, 2), P(-1, -2)), dm21 = p_sub(P(1, -2), P(-1, 2));
-  const V d22 = p_sub(P(2, 2), P(-2, -2)), dm22 = p_sub(P(2, -2), P(-2, 2));
-  const V a1 = v2<C>(kp.a1[0], kp.a1[1]), a2 = v2<C>(kp.a2[0], kp.a2[1]);
-  const V a4 = v2<C>(kp.a4x2[0], kp.a4x2[1]), a5 = v2<C>(kp.a5[0], kp.a5[1]);
-  const V a8 = v2<C>(kp.a8x2[0], kp.a8x2[1]), two = splat<C>(C(2));
-  // x: a1 d10 + a2 (d11 - dm1) + 2 a4 d20 + a5 (d12 - dm12 + 2 (d21 - dm21)) + 2 a8 (d22 - dm22)
-  V t = p_mul(a1, d10);
-  t = p_fma(a2, p_sub(d11, dm1), t);
-  t = p_fma(a4, d20, t);
-  t = p_fma(a5, p_fma(two, p_sub(d21, dm21), p_sub(d12, dm12)), t);
-  sx = p_fma(a8, p_sub(d22, dm22), t);
-  // y: a1 d01 + a2 (d11 + dm1) + 2 a4 d02 + a5 (2 (d12 + dm12) + d21 + dm21) + 2 a8 (d22 + dm22)
-  t = p_mul(a1, d01);
-  t = p_fma(a2, p_add(d11, dm1), t);
-  t = p_fma(a4, d02, t);
-  t = p_fma(a5, p_fma(two, p_add(d12, dm12), p_add(d21, dm21)), t);
-  sy = p_fma(a8, p_add(d22, dm22), t);
-  psl = P(0, 0);
-  const V npsl = p_mul(psl, splat<C>(C(-1)));
-  const V gr = p_mul(splat<C>(-kp.gx), r);
-  Fx = p_fma(r, splat<C>(kp.body_fx), p_fma(npsl, sx, p_mul(gr, crx)));
-  Fyp = p_fma(npsl, sy, p_mul(gr, cry));
+  StencilSums<C> a;
+  V pu[5], pd[5], ru[3], rd[3];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) pu[k] = sm.psi[cy][cx + k - 2];
+  sums_row0<C>(a, kp, pu, sm.rho[cy][cx - 1], sm.rho[cy][cx + 1]);
+  psl = pu[2];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    pu[k] = sm.psi[cy + 1][cx + k - 2];
+    pd[k] = sm.psi[cy - 1][cx + k - 2];
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    ru[k] = sm.rho[cy + 1][cx + k - 1];
+    rd[k] = sm.rho[cy - 1][cx + k - 1];
+  }
+  sums_row1<C>(a, kp, pu, pd, ru, rd);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    pu[k] = sm.psi[cy + 2][cx + k - 2];
+    pd[k] = sm.psi[cy - 2][cx + k - 2];
+  }
+  sums_row2<C>(a, kp, pu, pd);
+  sums_forces<C>(a, kp, r, psl, Fx, Fyp, crx, cry);
+  sx = a.sx;
+  sy = a.sy;
 }
 
 // Fy of both components: the interaction part plus the buoyancy rho_l alpha_g T of Eq. alphaG.
@@ -520,12 +582,22 @@ __device__ __forceinline__ void node_forces(const SM& sm, const KParams<C>& kp, 
 
 // Reciprocals of rho_1, rho_2 and rho_1 + rho_2 from one division.
 template <class C> __device__ __forceinline__ void three_reciprocals(C r1, C r2, C& i1, C& i2, C& irho) {
-  const C rho = r1 + r2;
-  const C p12 = r1 * r2;
-  const C inv = recip<C>(p12 * rho);
-  i1 = r2 * rho * inv;
-  i2 = r1 * rho * inv;
-  irho = p12 * inv;
+  const C rho = s_add(r1, r2);
+  const C p12 = s_mul(r1, r2);
+  const C inv = recip<C>(s_mul(p12, rho));
+  i1 = s_mul(s_mul(r2, rho), inv);
+  i2 = s_mul(s_mul(r1, rho), inv);
+  irho = s_mul(p12, inv);
+}
+
+// Velocities of a node (Eq. velo, u^(H) = u + F / (2 rho)) from its bare momentum and total forces.
+template <class C>
+__device__ __forceinline__ void node_velocities(C jx, C jy, C inv_rho, const C Fx[2], const C Fy[2], C& ux, C& uy,
+                                                C& uHx, C& uHy) {
+  ux = s_mul(jx, inv_rho);
+  uy = s_mul(jy, inv_rho);
+  uHx = s_fma(s_mul(C(0.5), s_add(Fx[0], Fx[1])), inv_rho, ux);
+  uHy = s_fma(s_mul(C(0.5), s_add(Fy[0], Fy[1])), inv_rho, uy);
 }
 
 // BGK relaxation of the 27 populations of one node (Eqs. BGK, LBMg, Teq); in shifted storage the
@@ -574,13 +646,13 @@ template <class C, bool SHIFT, bool RELAX>
 __device__ __forceinline__ void collide_thermal(const KParams<C>& kp, const C g[9], C T, C dT, C uHx, C uHy,
                                                 C post[27]) {
   using V = V2<C>;
-  const C nusq = C(-1.5) * (uHx * uHx + uHy * uHy);
+  const C nusq = s_mul(C(-1.5), s_fma(uHx, uHx, s_mul(uHy, uHy)));
   const C base = SHIFT ? dT : T;
   const V vn = splat<C>(nusq), vT = splat<C>(T), vb = splat<C>(base), k45 = splat<C>(C(4.5));
   const V pm3 = v2<C>(C(3), C(-3));
-  const C g0 = wq<C>(0) * (base + T * nusq);
-  post[18] = RELAX ? g[0] + (g0 - g[0]) * kp.inv_tau_g : g0;
-  const C cus[4] = {uHx, uHy, uHx + uHy, uHy - uHx};
+  const C g0 = s_mul(wq<C>(0), s_fma(T, nusq, base));
+  post[18] = RELAX ? s_fma(s_add(g0, -g[0]), kp.inv_tau_g, g[0]) : g0;
+  const C cus[4] = {uHx, uHy, s_add(uHx, uHy), s_add(uHy, -uHx)};
   const int dir[4] = {1, 2, 5, 6};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -664,6 +736,45 @@ __device__ __forceinline__ void push_store(SF<S>* __restrict__ fout, const KPara
   }
 }
 
+// Moments of a fluid node (Sec. 2.1, 2.3): densities and bare momentum from phase A, T from its thermal
+// populations; in shifted storage the sums are deviations from the shift.
+template <class C> struct NodeMoments {
+  C dr1, dr2, r1, r2, dT, T, jx, jy;
+};
+template <class C, bool SHIFT, class SMT>
+__device__ __forceinline__ NodeMoments<C> node_moments(const SMT& sm, const KParams<C>& kp, int tx, int ty,
+                                                       const C g[9]) {
+  NodeMoments<C> m;
+  m.dr1 = sm.rho[ty + 2][tx + 2].x;
+  m.dr2 = sm.rho[ty + 2][tx + 2].y;
+  m.r1 = SHIFT ? m.dr1 + kp.rho_bar[0] : m.dr1;
+  m.r2 = SHIFT ? m.dr2 + kp.rho_bar[1] : m.dr2;
+  m.dT = C(0);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) m.dT += g[i];
+  m.T = m.dT + (SHIFT ? kp.T_bar : C(0));
+  m.jx = sm.jx[ty][tx];
+  m.jy = sm.jy[ty][tx];
+  return m;
+}
+
+// The rest of a fluid node's step once its moments and interaction forces (Fx, and Fyp without the
+// buoyancy) are known: buoyancy, velocities (Eq. velo, Eq. shift, u^(H) = u + F / (2 rho)), BGK
+// collisions and the push store.
+template <class S, class C, bool SHIFT, bool FAST, class SMT>
+__device__ __forceinline__ void step_finish(SF<S>* __restrict__ fout, const KParams<C>& kp, const SMT& sm,
+                                            const C f[9], const C h[9], const C g[9], const NodeMoments<C>& m,
+                                            int tx, int ty, int gx, int gy, int idx, V2<C> Fx2, V2<C> Fyp) {
+  const V2<C> Fy2 = buoyant_fy<C>(kp, Fyp, v2<C>(m.r1, m.r2), m.T);
+  const C Fx[2] = {Fx2.x, Fx2.y}, Fy[2] = {Fy2.x, Fy2.y};
+  C i1, i2, inv_rho, ux, uy, uHx, uHy;
+  three_reciprocals<C>(m.r1, m.r2, i1, i2, inv_rho);
+  node_velocities<C>(m.jx, m.jy, inv_rho, Fx, Fy, ux, uy, uHx, uHy);
+  C post[27];
+  node_collide<C, SHIFT>(kp, f, h, g, m.r1, m.r2, m.dr1, m.dr2, m.T, m.dT, ux, uy, i1, i2, Fx, Fy, uHx, uHy, post);
+  push_store<S, C, FAST>(fout, kp, idx, gx, gy, post, sm.solid, tx + 2, ty + 2, m.r1, m.r2);
+}
+
 // Phase B on one tile.  MODE_STEP: collide and push-store; MODE_OBS: accumulate the observables
 // of the node into acc[]; MODE_FIELDS: write rho1, rho2, T, u^(H) to aux planes.
 template <class S, class C, bool SHIFT, int MODE, bool FAST, int TX, int TY, int BY, class Src>
@@ -671,7 +782,6 @@ __device__ __forceinline__ void tile_phase_b(const Src& pop, SF<S>* __restrict__
                                              const TileSmem<C, TX, TY, MODE != MODE_STEP>& sm, double* __restrict__ aux,
                                              double acc[kObsSlots]) {
   const int nx = kp.nx, ny = kp.ny, pitch = kp.pitch, plane = kp.plane;
-  const C Tb = SHIFT ? kp.T_bar : C(0);
 #pragma unroll 1
   for (int k = 0; k < TY / BY; ++k) {
     const int tx = threadIdx.x, ty = threadIdx.y + k * BY;
@@ -703,22 +813,21 @@ __device__ __forceinline__ void tile_phase_b(const Src& pop, SF<S>* __restrict__
         h[i] = C(pop(9 + i, idx, tx, ty));
       }
     }
-    const C dr1 = sm.rho[cy][cx].x, dr2 = sm.rho[cy][cx].y;
-    const C r1 = SHIFT ? dr1 + kp.rho_bar[0] : dr1, r2 = SHIFT ? dr2 + kp.rho_bar[1] : dr2;
-    C dT = C(0);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) dT += g[i];
-    const C T = dT + Tb;
-    const C jx = sm.jx[ty][tx], jy = sm.jy[ty][tx];
-    C Fx[2], Fy[2];
-    node_forces<C>(sm, kp, cx, cy, r1, r2, T, Fx, Fy);
+    const NodeMoments<C> m = node_moments<C, SHIFT>(sm, kp, tx, ty, g);
+    const C dr1 = m.dr1, dr2 = m.dr2, r1 = m.r1, r2 = m.r2, dT = m.dT, T = m.T;
+    V2<C> fx2, fyp2, q0, q1, q2, q3, q4;
+    node_force_pair<C>(sm, kp, cx, cy, v2<C>(r1, r2), fx2, fyp2, q0, q1, q2, q3, q4);
+    if constexpr (MODE == MODE_STEP) {
+      step_finish<S, C, SHIFT, FAST>(fout, kp, sm, f, h, g, m, tx, ty, gx, gy, idx, fx2, fyp2);
+      continue;
+    }
+    const V2<C> fy2 = buoyant_fy<C>(kp, fyp2, v2<C>(r1, r2), T);
+    const C Fx[2] = {fx2.x, fx2.y}, Fy[2] = {fy2.x, fy2.y};
     // velocities: Eq. velo, Eq. shift, u^(H) = u + F / (2 rho)
-    C i1, i2, inv_rho;
+    C i1, i2, inv_rho, ux, uy, uHx, uHy;
     three_reciprocals<C>(r1, r2, i1, i2, inv_rho);
+    node_velocities<C>(m.jx, m.jy, inv_rho, Fx, Fy, ux, uy, uHx, uHy);
     const C rho = r1 + r2;
-    const C ux = jx * inv_rho, uy = jy * inv_rho;
-    const C uHx = ux + C(0.5) * (Fx[0] + Fx[1]) * inv_rho;
-    const C uHy = uy + C(0.5) * (Fy[0] + Fy[1]) * inv_rho;
 
     if constexpr (MODE == MODE_OBS) {
       const C Tup = sm.solid[cy + 1][cx] ? C(2) * sm.T[cy + 1][cx] - T : sm.T[cy + 1][cx];
@@ -758,10 +867,6 @@ __device__ __forceinline__ void tile_phase_b(const Src& pop, SF<S>* __restrict__
       aux[2 * N + n] = (double)T;
       aux[3 * N + n] = (double)uHx;
       aux[4 * N + n] = (double)uHy;
-    } else {
-      C post[27];
-      node_collide<C, SHIFT>(kp, f, h, g, r1, r2, dr1, dr2, T, dT, ux, uy, i1, i2, Fx, Fy, uHx, uHy, post);
-      push_store<S, C, FAST>(fout, kp, idx, gx, gy, post, sm.solid, cx, cy, r1, r2);
     }
   }
 }

@@ -77,11 +77,9 @@ __device__ __forceinline__ void stream_node(const float* __restrict__ fin, float
   const float jx = w.jx[cy][cx - 2], jy = w.jy[cy][cx - 2];
   float Fx[2], Fy[2];
   node_forces<float>(w, kp, cx, cy, r1, r2, T, Fx, Fy);
-  float i1, i2, inv_rho;
+  float i1, i2, inv_rho, ux, uy, uHx, uHy;
   three_reciprocals<float>(r1, r2, i1, i2, inv_rho);
-  const float ux = jx * inv_rho, uy = jy * inv_rho;
-  const float uHx = ux + 0.5f * (Fx[0] + Fx[1]) * inv_rho;
-  const float uHy = uy + 0.5f * (Fy[0] + Fy[1]) * inv_rho;
+  node_velocities<float>(jx, jy, inv_rho, Fx, Fy, ux, uy, uHx, uHy);
   float post[27];
   node_collide<float, true>(kp, f, h, g, r1, r2, dr1, dr2, T, dT, ux, uy, i1, i2, Fx, Fy, uHx, uHy, post);
   push_store<float, float, FAST, kSRX>(fout, kp, idx, gx, gy, post, w.solid, cx, cy, r1, r2);
