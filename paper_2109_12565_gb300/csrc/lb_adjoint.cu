@@ -166,7 +166,7 @@ lb_adj1_kernel(const S* __restrict__ fin, const S* __restrict__ lam_out, S* __re
       lT += cJ * uHy * nuc;
       const int up = (sm.solid[cy + 1][cx] && 2 * (gy + 1) < ny) ? 1 : 0;
       const int dn = (sm.solid[cy - 1][cx] && 2 * (gy - 1) < ny) ? 1 : 0;
-      dtd += (double)cJ * mirror_coef * (double)(up - dn);
+      if (up != dn) dtd += (double)cJ * mirror_coef * (double)(up - dn);  // zero away from the walls
     }
     // u^(H) = u + F / (2 rho)
     lux += luHx;
@@ -207,7 +207,9 @@ lb_adj1_kernel(const S* __restrict__ fin, const S* __restrict__ lam_out, S* __re
     lamF[2 * plane + idx] = S(lFx[1]);
     lamF[3 * plane + idx] = S(lFy[1]);
   }
-  // per-block dJ/dT_down, added to this block's running total (one writer per slot, stream order)
+  // per-block dJ/dT_down, added to this block's running total (one writer per slot, stream order);
+  // only blocks next to a wall have a nonzero share
+  if (!__syncthreads_or(dtd != 0.0)) return;
   __shared__ double s_red[NT / 32];
   const double v = warp_sum(dtd);
   if ((tid & 31) == 0) s_red[tid >> 5] = v;

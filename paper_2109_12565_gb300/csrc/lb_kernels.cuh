@@ -22,6 +22,10 @@
 // wrap takes a fast path: every store is an unconditional constant offset.
 // Writes of direction i from a warp land on one contiguous row shifted by
 // c_i; each destination slot has exactly one writer per step.
+// Shared memory holds the two components of a node in one slot, and the hot
+// arithmetic runs on lane pairs (components, opposite directions, or the two
+// nodes of a phase-A pair): packed FP32x2 instructions in FP32, one FP64
+// instruction per lane in FP64, each rounding once.
 #pragma once
 #include <cuda_fp16.h>
 #include <math.h>
