@@ -191,8 +191,6 @@ template <class C> __device__ __forceinline__ V2<C> v2(C a, C b) {
   r.y = b;
   return r;
 }
-// component l of an interleaved pair (l is a compile-time constant after unrolling)
-template <class V> __device__ __forceinline__ auto comp(const V& v, int l) -> decltype(v.x) { return l ? v.y : v.x; }
 template <class C> __device__ __forceinline__ V2<C> splat(C a) { return v2<C>(a, a); }
 template <class V> __device__ __forceinline__ V swap_lanes(const V& v) {
   V r;
