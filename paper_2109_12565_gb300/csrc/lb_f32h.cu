@@ -23,6 +23,8 @@ const Cand kCands[] = {
     {{64, 32, 8, 2}, launch_step_shape<F32H16, true, 64, 32, 8, 2>},
     {{32, 16, 8, 3}, launch_step_shape<F32H16, true, 32, 16, 8, 3>},
     {{32, 8, 8, 4}, launch_step_shape<F32H16, true, 32, 8, 8, 4>},
+    // 32 x 9: 1824 tiles at 1024 x 512, exactly three waves of 4 CTAs (56 registers) on 152 SMs
+    {{32, 9, 9, 4}, launch_step_shape<F32H16, true, 32, 9, 9, 4>},
 };
 }  // namespace
 
