@@ -249,7 +249,8 @@ def test_fp32_shifted_state_roundtrip():
     assert np.abs(g.get_state() - o.state).max() <= 1e-7
 
 
-@pytest.mark.parametrize("precision,steps,tol", [(lb.LB_FP64, 12, 1e-12), (lb.LB_FP32_SHIFTED, 12, 1e-4)])
+@pytest.mark.parametrize("precision,steps,tol", [(lb.LB_FP64, 12, 1e-12), (lb.LB_FP32_SHIFTED, 12, 1e-4),
+                                                 (lb.LB_FP32_FP16T, 12, FP16T_T_TOL)])
 def test_full_size_1024x512_against_oracle(precision, steps, tol):
     """The 1024 x 512 concentrated emulsion in the launch configuration the benchmark times, checked
     against the oracle on every node (the OpenMP oracle finishes this in seconds)."""
