@@ -176,11 +176,13 @@ int lb_tile_info(const lb_handle* h, int candidate, int* tx, int* ty, int* threa
  * stream: cudaStream_t or NULL; the call synchronises it.
  * Scratch: a 2 MiB file-scope device array that every GPU loading the library holds until exit;
  * lattices needing more than 21,844 tiles of 32 x 16 nodes are rejected with LB_EINVAL before any
- * launch (4096 x 2720 fits, 4096 x 2736 does not).  The first call on a device looks the array up
- * (cudaGetSymbolAddress) and must come before any stream capture.  All calls on a device share the
- * array: calls that overlap on the GPU race and must be serialised by the caller.  Allocates
- * nothing.  Returns LB_OK, LB_EUNSTABLE (out filled), LB_EINVAL or LB_ECUDA; lb_last_error is not
- * updated. */
+ * launch (4096 x 2720 fits, 4096 x 2736 does not).  With CUDA's lazy module loading the array is
+ * created by the first call on a device, so make one warm-up call at initialisation, before any
+ * stream capture; later calls allocate nothing.  Every call looks the array's device address up
+ * afresh (cudaGetSymbolAddress), so a device reset between calls is harmless.  All calls on a device
+ * share the array: calls that overlap on the GPU race and must be serialised by the caller.
+ * Returns LB_OK, LB_EUNSTABLE (out filled), LB_EINVAL (bad parameters, d_state not 8-byte aligned,
+ * lattice too large) or LB_ECUDA; lb_last_error is not updated. */
 int lb_observables_static(const lb_params* p, const double* d_state, const uint8_t* d_mask, lb_obs* out,
                           void* stream);
 

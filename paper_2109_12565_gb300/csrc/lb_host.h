@@ -4,6 +4,7 @@
 #pragma once
 #include <cmath>
 #include <cstddef>
+#include <cstdio>
 
 #include "lb_cfg.h"
 #include "tlb.h"
