@@ -44,7 +44,10 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS and % of HBM roofline: FP64 vs FP32-shifted vs batched; adjoint/forward cost"
 FLUSH_BYTES = 512 << 20
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate
+# FP64 (non-tensor) peak from the unit counts and the clock: 152 SMs x 2 FP64 FMA per clock per SM
+# x 2 flops per FMA x the maximum SM clock (MEASURED_PEAKS.json sm_max_mhz, else 2070 MHz).
+FP64_SMS, FP64_FMA_PER_CLK_PER_SM = 152, 2
+DETAIL_DEFAULT = os.path.join("gpurun_out", "bench_detail.json")
 
 
 def _peaks():
@@ -54,6 +57,28 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return PEAKS_FALLBACK["hbm_gbs"], "fallback"
+
+
+def fp64_peak_tflops():
+    """FP64 FMA-pipe peak of the GPU from its unit counts and maximum SM clock."""
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mhz = float(json.load(fh).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return FP64_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def rnd(v, digits=5):
+    """Round floats (recursively) to `digits` significant digits to keep the JSON line short."""
+    if isinstance(v, float):
+        return float(f"{v:.{digits}g}") if v == v and abs(v) != float("inf") else v
+    if isinstance(v, dict):
+        return {k: rnd(x, digits) for k, x in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [rnd(x, digits) for x in v]
+    return v
 
 
 # sources that define the step kernels (their DRAM counters go stale when one of these changes)
@@ -213,8 +238,8 @@ def time_form(w, precision, steps, warmup, flush, tile=-1):
     g.close()
     return {"ms_total": sum(times), "ms_per_step": sum(times) / steps, "ms_min": min(times),
             "ms_median": statistics.median(times), "obs": obs,
-            "tile": {"candidate": tile, "tx": shape["tx"], "ty": shape["ty"], "threads": shape["threads"],
-                     "autotune_ms_per_candidate": [round(m, 5) for m in cand_ms]}}
+            "tile": {"candidate": tile, "tx": shape["tx"], "ty": shape["ty"], "threads": shape["threads"]},
+            "autotune_ms_per_candidate": [round(m, 5) for m in cand_ms]}
 
 
 def time_batch(reps, steps, warmup, trial_steps=16):
@@ -416,6 +441,8 @@ def main():
                     help="fixed tile candidate (index within the precision's own list) instead of autotuning")
     ap.add_argument("--batch-steps", type=int, default=200, help="timed steps of the 64-replica ensemble")
     ap.add_argument("--adjoint-steps", type=int, default=2000, help="N of the adjoint gradient (512 x 256)")
+    ap.add_argument("--detail", default=DETAIL_DEFAULT,
+                    help="file for the per-candidate autotuner timings and other detail kept off the JSON line")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -481,7 +508,12 @@ def main():
     peak, peak_kind = _peaks()
     prof = _profile_counters()
     bytes32, bytes64 = 216.0 * N, 432.0 * N  # 27 populations read + written per node
-    forms = {}
+    forms, detail = {}, {}
+
+    def tile_of(r):
+        t = r["tile"]
+        return f'{t["tx"]}x{t["ty"]}/{t["threads"]}#{t["candidate"]}'
+
     roof = None
     if r32:
         ach32 = bytes32 / (r32["ms_per_step"] * 1e-3) / 1e9
@@ -489,51 +521,63 @@ def main():
                 "traffic": _traffic(prof, "fp32", r32["tile"]["candidate"]), "peak_source": peak_kind,
                 "kernel": "lb_step_kernel<float, shifted> (fused step)", "algorithmic_bytes_per_launch": bytes32}
         forms["fp32_shifted"] = {"MLUPS": mlups32, "ms_per_step": r32["ms_per_step"], "hbm_frac": ach32 / peak,
-                                 "GBps": ach32, "Nu": r32["obs"]["Nu"], "tile": r32["tile"]}
-    if r64:
-        ach64 = bytes64 / (r64["ms_per_step"] * 1e-3) / 1e9
-        forms["fp64"] = {"MLUPS": mlups64, "ms_per_step": r64["ms_per_step"], "hbm_frac": ach64 / peak,
-                         "GBps": ach64, "bound": "alu (FP64 pipe)",
-                         "traffic": _traffic(prof, "fp64", r64["tile"]["candidate"]), "Nu": r64["obs"]["Nu"],
-                         "tile": r64["tile"]}
-        dp = prof.get("fp64_dp_flops_per_node")
-        if dp:
-            forms["fp64"]["dp_tflops"] = dp * N / (r64["ms_per_step"] * 1e-3) / 1e12
-            forms["fp64"]["alu_frac_of_nominal"] = forms["fp64"]["dp_tflops"] / FP64_NOMINAL_TFLOPS
-    if r32 and r64:
-        forms["fp32_over_fp64"] = mlups32 / mlups64
+                                 "Nu": r32["obs"]["Nu"], "tile": tile_of(r32)}
+        detail["fp32_autotune_ms_per_candidate"] = r32["autotune_ms_per_candidate"]
     if r16:
         ach16 = 180.0 * N / (r16["ms_per_step"] * 1e-3) / 1e9  # 18 FP32 + 9 FP16 values read + written
         forms["fp32_fp16_thermal"] = {"MLUPS": aggregate_mlups(world, N, args.steps, t16),
-                                      "ms_per_step": r16["ms_per_step"],
-                                      "hbm_frac": ach16 / peak, "GBps": ach16, "bytes_per_update": 180,
+                                      "hbm_frac": ach16 / peak, "bytes_per_update": 180,
                                       "traffic": _traffic(prof, "fp16t", r16["tile"]["candidate"]),
-                                      "Nu": r16["obs"]["Nu"], "tile": r16["tile"]}
+                                      "Nu": r16["obs"]["Nu"], "tile": tile_of(r16)}
+        detail["fp16t_autotune_ms_per_candidate"] = r16["autotune_ms_per_candidate"]
     if rr:
         Nr = wr.params["nx"] * wr.params["ny"]
         achr = 216.0 * Nr / (rr["ms_per_step"] * 1e-3) / 1e9
-        forms["rough_channel_4096x2048"] = {"MLUPS": aggregate_mlups(world, Nr, args.rough_steps, trr),
-                                            "ms_per_step": rr["ms_per_step"],
-                                            "hbm_frac": achr / peak, "GBps": achr, "steps": args.rough_steps,
-                                            "traffic": _traffic(prof, "rough_channel_fp32", rr["tile"]["candidate"]),
-                                            "precision": "fp32_shifted", "Nu": rr["obs"]["Nu"], "tile": rr["tile"]}
-    if rdrop:
-        step_ms = r32["ms_per_step"] if r32 else None
-        for k, v in rdrop.items():
-            if k == "emulsion_1024x512" and step_ms:
-                v["fp32_step_equivalents"] = v["ms"] / step_ms
-        forms["droplets"] = rdrop
-    if radj:
-        forms["adjoint"] = dict(workload="emulsion_512x256", **{k: v for k, v in radj.items()})
+        forms["rough_4096x2048"] = {"MLUPS": aggregate_mlups(world, Nr, args.rough_steps, trr),
+                                    "hbm_frac": achr / peak,
+                                    "traffic": _traffic(prof, "rough_channel_fp32", rr["tile"]["candidate"]),
+                                    "tile": tile_of(rr)}
+        detail["rough_autotune_ms_per_candidate"] = rr["autotune_ms_per_candidate"]
     if rb:
         achb = 216.0 * rb["nodes"] / (rb["ms_per_step"] * 1e-3) / 1e9
         forms["batched"] = {"MLUPS": aggregate_mlups(world, rb["nodes"], args.batch_steps, tb), "replicas": len(ens),
-                            "nodes": rb["nodes"], "ms_per_step": rb["ms_per_step"], "hbm_frac": achb / peak,
-                            "GBps": achb, "schedule": ["per-step graph", "persistent"][rb["info"]["schedule"]],
-                            "tile_candidate": rb["info"]["tile"], "work_items": rb["info"]["items"],
-                            "persistent_grid": rb["info"]["grid"], "graphs": rb["info"]["graphs"],
-                            "autotune_ms_per_step": rb["tune"]["ms_per_step"], "steps": args.batch_steps,
-                            "Nu_replica0": rb["Nu_replica0"]}
+                            "nodes": rb["nodes"], "hbm_frac": achb / peak,
+                            "schedule": ["per-step graph", "persistent"][rb["info"]["schedule"]],
+                            "tile": rb["info"]["tile"]}
+        detail["batched"] = {"autotune_ms_per_step": rb["tune"]["ms_per_step"], "info": rb["info"],
+                             "Nu_replica0": rb["Nu_replica0"], "ms_per_step": rb["ms_per_step"]}
+    if radj:
+        forms["adjoint_512x256"] = {k: {"rev_over_fwd": v["adjoint_step_ms"] / v["forward_step_ms"],
+                                        "grad_over_fwd_run": v["amortised_over_forward"],
+                                        "fwd_step_ms": v["forward_step_ms"]} for k, v in radj.items()}
+        detail["adjoint"] = radj
+    if rdrop:
+        step_ms = r32["ms_per_step"] if r32 else None
+        forms["droplets_ms"] = {k: v["ms"] for k, v in rdrop.items()}
+        if step_ms:
+            forms["droplets_ms"]["fp32_steps_1024x512"] = rdrop["emulsion_1024x512"]["ms"] / step_ms
+        detail["droplets"] = rdrop
+    if r64:
+        # the paper's arithmetic: FP64 storage and FP64 arithmetic; bound by the FP64 pipe, not by HBM
+        ach64 = bytes64 / (r64["ms_per_step"] * 1e-3) / 1e9
+        f64 = {"MLUPS": mlups64, "ms_per_step": r64["ms_per_step"], "hbm_frac": ach64 / peak,
+               "Nu": r64["obs"]["Nu"], "tile": tile_of(r64)}
+        dp = prof.get("fp64_dp_flops_per_node")
+        pk = fp64_peak_tflops()
+        if dp:
+            ach_tf = dp * N / (r64["ms_per_step"] * 1e-3) / 1e12
+            f64["roofline"] = {"bound": "alu", "achieved": ach_tf, "peak": pk, "unit": "TFLOP/s",
+                               "frac": ach_tf / pk, "flops_per_node": dp,
+                               "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x sm_max_mhz"}
+        else:
+            f64["roofline"] = {"bound": "alu", "achieved": None, "peak": pk, "unit": "TFLOP/s", "frac": None,
+                               "flops_per_node": None, "note": "no ncu FP64 instruction count for these kernels"}
+        f64["hbm"] = {"achieved": ach64, "peak": peak, "unit": "GB/s", "frac": ach64 / peak,
+                      "traffic": _traffic(prof, "fp64", r64["tile"]["candidate"])}
+        if r32:
+            f64["fp32_over_fp64"] = mlups32 / mlups64
+        detail["fp64_autotune_ms_per_candidate"] = r64["autotune_ms_per_candidate"]
+        forms["fp64"] = f64  # last key of the line: it survives a truncated tail
     head = r32 or r64 or {"ms_per_step": None}
     line = {
         "metric": METRIC, "value": mlups32 if r32 else mlups64, "unit": "MLUPS", "n_gpus": world,
@@ -545,7 +589,6 @@ def main():
                    "l2": "flushed before every timed step (512 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
-        "forms": forms,
         "e2e": e2e,
         "gpu_launches": (args.steps if r32 else 0) + (steps64 if r64 else 0) + (args.steps if r16 else 0) + (
             args.rough_steps if rr else 0) + (
@@ -553,8 +596,19 @@ def main():
         "clocks": clk.summary(),
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, seconds=args.cpu_seconds)
-    print(json.dumps(line), flush=True)
+        cb = cpu_baseline(w, seconds=args.cpu_seconds)
+        detail["cpu_single_thread"] = cb.pop("single_thread")
+        line["cpu_baseline"] = cb
+    line["forms"] = forms
+    line = rnd(line)
+    if args.detail:
+        try:
+            os.makedirs(os.path.dirname(os.path.abspath(args.detail)), exist_ok=True)
+            with open(args.detail, "w") as fh:
+                json.dump(rnd(detail, 6), fh, indent=1)
+        except OSError:
+            pass
+    print(json.dumps(line, separators=(",", ":")), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
