@@ -59,6 +59,7 @@ def lib(omp=False):
         L.orc_fields.argtypes = [P, u8, dp, dp, dp, dp, dp, dp]
         L.orc_observables.argtypes = [P, u8, dp, dp]
         L.orc_wall_force.argtypes = [P, u8, dp, dp]
+        L.orc_stress.argtypes = [P, u8, dp, dp, dp, dp, dp]
         L.orc_adjoint_step.argtypes = [P, u8, dp, dp, ctypes.c_double, dp, dp]
         L.orc_adjoint_run.argtypes = [P, u8, dp, dp, dp, ctypes.c_long, dp, dp, dp]
         ip = ctypes.POINTER(ctypes.c_int)
@@ -67,7 +68,7 @@ def lib(omp=False):
         L.orc_digital_voronoi.argtypes = [P, u8, dp, dp, ctypes.c_int, ip]
         L.orc_voronoi_links.argtypes = [P, ip, ip, ctypes.c_long, ctypes.POINTER(ctypes.c_long)]
         for f in ("orc_solid_map", "orc_init", "orc_forces", "orc_step", "orc_run", "orc_fields",
-                  "orc_observables", "orc_wall_force", "orc_adjoint_step", "orc_adjoint_run", "orc_droplet_labels",
+                  "orc_observables", "orc_wall_force", "orc_stress", "orc_adjoint_step", "orc_adjoint_run", "orc_droplet_labels",
                   "orc_droplet_centres", "orc_digital_voronoi", "orc_voronoi_links"):
             getattr(L, f).restype = ctypes.c_int
         _LIBS[key] = L
@@ -222,6 +223,35 @@ def adjoint_run(params, rho1, rho2, T0, nsteps, mask=None):
     _check(lib().orc_adjoint_run(ctypes.byref(cp), mp, _dp(r1), _dp(r2), _dp(t0), int(nsteps), ctypes.byref(J),
                                  _dp(dT0), ctypes.byref(dTd)), "adjoint_run")
     return J.value, dT0, dTd.value
+
+
+def stress(params, state, mask=None):
+    """Total shear stress of the state S_t (see orc_stress): dict with the means over fluid nodes of
+    sigma_xy ("Sigma"), of the viscous part ("visc"), of the interaction pressure tensor P^int_xy
+    ("pint") and of the forcing part P^F_xy ("pforce"), the per-row means "row" [ny], and the fields
+    "sxy", "pint_field" [ny, nx]."""
+    cp = make_params(params)
+    ny, nx = int(params["ny"]), int(params["nx"])
+    st = np.ascontiguousarray(state, dtype=np.float64)
+    sxy, pint, row, out = np.zeros((ny, nx)), np.zeros((ny, nx)), np.zeros(ny), np.zeros(4)
+    m, mp = _mask(mask)
+    _check(lib().orc_stress(ctypes.byref(cp), mp, _dp(st), _dp(sxy), _dp(pint), _dp(row), _dp(out)), "stress")
+    return {"Sigma": out[0], "visc": out[1], "pint": out[2], "pforce": out[3], "row": row, "sxy": sxy,
+            "pint_field": pint}
+
+
+def nusselt_mean(params, rho1, rho2, T0, nsteps, mask=None, omp=False):
+    """J = (1/N) sum_{t=1..N} Nu(S_t) (Eq. NuTime) from the rest-equilibrium start of (rho1, rho2, T0):
+    the forward half of ``adjoint_run`` alone (one step, then the observables of the new state, N
+    times), without storing the states."""
+    o = Oracle(params, rho1, rho2, T0, mask=mask, omp=omp)
+    out = np.zeros(8)
+    s = 0.0
+    for _ in range(int(nsteps)):
+        o.step(1)
+        _check(o.L.orc_observables(ctypes.byref(o.cp), o._mask_ptr, _dp(o.state), _dp(out)), "observables")
+        s += out[4]
+    return s / float(nsteps)
 
 
 def _ip(a):

@@ -471,6 +471,129 @@ int orc_observables(const orc_params* prm, const uint8_t* mask, const double* st
 }
 
 /* ======================================================================================
+ * Total shear stress of the rheology experiment (Sec. 2.1, text after Eq. NS; Sec. 3.2.1).
+ *
+ * The total stress is the bare viscous stress eta_0 (d_i u^(H)_j + d_j u^(H)_i), Eq. (VISCO):
+ * eta_0 = rho c_s^2 (tau - 1/2), supplemented by the pressure tensor P_ij of the model.
+ * The xy component at a fluid node x:
+ *   sigma_xy(x) = eta_0(x) (d_x u^(H)_y + d_y u^(H)_x) - P^int_xy(x) - P^F_xy(x)
+ * with central differences; a solid neighbour takes the mirror value 2 u_w - u(x) (u_w: the wall
+ * velocity along x of a flat wall row, 0 for the y component and for obstacles).
+ *   P^int: the virial form of the pair forces of Eqs. (FAB), (FintAttrattive), (FintRepulsive): a
+ *          force -G psi(x) sum_i W_i psi(x + c_i) c_i contributes (G / 2) psi(x) sum_i W_i
+ *          psi(x + c_i) c_ix c_iy, i.e. half of every pair term, so that the pair's two ends together
+ *          carry it once.  Solid and out-of-domain positions carry the wall pseudo-potentials.
+ *   P^F:   the momentum flux the forcing of Eq. (shift) adds: the equilibria carry
+ *          sum_l rho_l u_l u_l with u_l = u + tau F_l / rho_l, which exceeds rho u^(H) u^(H) (plus the
+ *          terms of the viscous stress) by tau^2 sum_l F_l F_l / rho_l - F F / (4 rho), F_l the total
+ *          force on component l (interaction and external), F = F_1 + F_2.
+ * ====================================================================================== */
+
+/* x or y component (comp 0 / 1) of u^(H) at neighbour (xn, yn) of fluid node (x, y), with the mirror
+ * rule at a solid neighbour. */
+static double u_neighbour(const orc_params* prm, const uint8_t* solid, const double* u, int comp, int x, int y,
+                          int xn, int yn) {
+  const int nx = prm->nx, ny = prm->ny;
+  xn = wrap(xn, nx);
+  if (prm->periodic_y) yn = wrap(yn, ny);
+  const double own = u[(long)y * nx + x];
+  if (yn < 0 || yn >= ny || solid[(long)yn * nx + xn]) {
+    const double uw = comp == 0 ? wall_u(prm, yn) : 0.0;
+    return 2.0 * uw - own;
+  }
+  return u[(long)yn * nx + xn];
+}
+
+int orc_stress(const orc_params* prm, const uint8_t* mask, const double* state, double* sxy, double* pint, double* row,
+               double* out4) {
+  if (!valid(prm)) return -1;
+  const int nx = prm->nx, ny = prm->ny;
+  const long N = (long)nx * ny;
+  uint8_t* solid = (uint8_t*)malloc((size_t)N);
+  double* buf = (double*)malloc(sizeof(double) * 13 * (size_t)N);
+  double *rho1 = buf, *rho2 = buf + N, *T = buf + 2 * N, *ux = buf + 3 * N, *uy = buf + 4 * N;
+  double* psit[2] = {buf + 5 * N, buf + 6 * N};
+  double* psie[2] = {buf + 7 * N, buf + 8 * N};
+  double* F = buf + 9 * N; /* [l][xy][N], Eqs. (FAB), (FintAttrattive), (FintRepulsive), (alphaG) */
+  orc_solid_map(prm, mask, solid);
+  fields_full(prm, solid, state, rho1, rho2, T, ux, uy);
+  forces_from_fields(prm, solid, rho1, rho2, T, F);
+  const double* rho[2] = {rho1, rho2};
+  double psit_w[2], psie_w[2];
+  for (int l = 0; l < 2; ++l) {
+    for (long n = 0; n < N; ++n) {
+      psit[l][n] = rho[l][n] / prm->rho0;
+      psie[l][n] = psi_exp(rho[l][n], prm->rho0);
+    }
+    psit_w[l] = prm->rho_wall[l] / prm->rho0;
+    psie_w[l] = psi_exp(prm->rho_wall[l], prm->rho0);
+  }
+  double sum_s = 0.0, sum_v = 0.0, sum_p = 0.0, sum_f = 0.0, nf = 0.0;
+  for (int y = 0; y < ny; ++y) {
+    double rs = 0.0, rn = 0.0;
+    for (int x = 0; x < nx; ++x) {
+      const long n = (long)y * nx + x;
+      if (solid[n]) {
+        if (sxy) sxy[n] = 0.0;
+        if (pint) pint[n] = 0.0;
+        continue;
+      }
+      /* bare viscous stress, Eq. (VISCO) with c_s^2 = 1/3 */
+      const double eta0 = (rho1[n] + rho2[n]) * (prm->tau - 0.5) / 3.0;
+      const double dvdx = 0.5 * (u_neighbour(prm, solid, uy, 1, x, y, x + 1, y) -
+                                 u_neighbour(prm, solid, uy, 1, x, y, x - 1, y));
+      const double dudy = 0.5 * (u_neighbour(prm, solid, ux, 0, x, y, x, y + 1) -
+                                 u_neighbour(prm, solid, ux, 0, x, y, x, y - 1));
+      const double visc = eta0 * (dvdx + dudy);
+      /* pressure tensor of the interaction forces, virial form */
+      double p = 0.0;
+      for (int l = 0; l < 2; ++l) {
+        const int m = 1 - l;
+        double sx = 0.0, sa = 0.0, sr = 0.0;
+        for (int i = 0; i < 9; ++i) { /* Eq. (FAB) and Eq. (FintAttrattive): NN links, weights w_i */
+          const double cc = (double)(CX[i] * CY[i]);
+          sx += weight_w(i) * field_at(prm, solid, psit[m], psit_w[m], x + CX[i], y + CY[i]) * cc;
+          sa += weight_w(i) * field_at(prm, solid, psie[l], psie_w[l], x + CX[i], y + CY[i]) * cc;
+        }
+        for (int i = 0; i < 25; ++i) { /* Eq. (FintRepulsive): NN and NNN links, weights p_i */
+          const double cc = (double)(CX[i] * CY[i]);
+          sr += weight_p(i) * field_at(prm, solid, psie[l], psie_w[l], x + CX[i], y + CY[i]) * cc;
+        }
+        p += 0.5 * prm->G12 * psit[l][n] * sx;
+        p += 0.5 * prm->Ga[l] * psie[l][n] * sa;
+        p += 0.5 * prm->Gr[l] * psie[l][n] * sr;
+      }
+      /* forcing part, Eq. (shift) */
+      double pf = 0.0;
+      for (int l = 0; l < 2; ++l)
+        pf += prm->tau * prm->tau * F[((long)l * 2 + 0) * N + n] * F[((long)l * 2 + 1) * N + n] / rho[l][n];
+      const double Fx = F[0 * N + n] + F[2 * N + n], Fy = F[1 * N + n] + F[3 * N + n];
+      pf -= Fx * Fy / (4.0 * (rho1[n] + rho2[n]));
+      const double s = visc - p - pf;
+      if (sxy) sxy[n] = s;
+      if (pint) pint[n] = p;
+      rs += s;
+      rn += 1.0;
+      sum_s += s;
+      sum_v += visc;
+      sum_p += p;
+      sum_f += pf;
+      nf += 1.0;
+    }
+    if (row) row[y] = rn > 0.0 ? rs / rn : 0.0;
+  }
+  if (out4) {
+    out4[0] = nf > 0.0 ? sum_s / nf : 0.0;
+    out4[1] = nf > 0.0 ? sum_v / nf : 0.0;
+    out4[2] = nf > 0.0 ? sum_p / nf : 0.0;
+    out4[3] = nf > 0.0 ? sum_f / nf : 0.0;
+  }
+  free(buf);
+  free(solid);
+  return 0;
+}
+
+/* ======================================================================================
  * Discrete adjoint (reverse mode) of the step and of the time-averaged Nusselt number
  * J = (1/N) sum_{t=1..N} Nu(S_t)  (Eq. NuTime), w.r.t. the initial temperature field and T_down.
  *

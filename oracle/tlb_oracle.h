@@ -90,6 +90,17 @@ int orc_fields(const orc_params* prm, const uint8_t* mask, const double* state, 
  * nodes with a non-finite or non-positive density, out[7] number of fluid nodes. */
 int orc_observables(const orc_params* prm, const uint8_t* mask, const double* state, double* out);
 
+/* Total shear stress of S_t (Sec. 2.1 after Eq. NS, Sec. 3.2.1): at every fluid node
+ * sigma_xy = eta_0 (d_x u^(H)_y + d_y u^(H)_x) - P^int_xy - P^F_xy, eta_0 = rho (tau - 1/2) / 3
+ * (Eq. VISCO), central differences with the mirror 2 u_w - u at a solid neighbour, P^int_xy the virial
+ * form of the interaction forces (half of every pair term of Eqs. FAB, FintAttrattive, FintRepulsive
+ * times c_ix c_iy), P^F_xy = tau^2 sum_l F_lx F_ly / rho_l - F_x F_y / (4 rho) the momentum flux of the
+ * forcing of Eq. shift.  sxy (sigma_xy), pint (P^int_xy) (nx*ny, 0 at solid nodes) and row (ny: mean
+ * of sigma_xy over the row's fluid nodes, the x-wise average) may be NULL; out4 (may be NULL): means
+ * over fluid nodes of sigma_xy, of the viscous part, of P^int_xy and of P^F_xy. */
+int orc_stress(const orc_params* prm, const uint8_t* mask, const double* state, double* sxy, double* pint,
+               double* row, double* out4);
+
 /* Discrete adjoint of one step (reverse mode): lam_in = (dS_{t+1}/dS_t)^T lam_out + cJ dNu(S_t)/dS_t,
  * where S is the state S_t and lam_out (may be NULL = 0) the adjoint of S_{t+1}; all in the state
  * layout.  *dJ_dTdown (may be NULL) is incremented by lam_out . dS_{t+1}/dT_down + cJ dNu(S_t)/dT_down. */
