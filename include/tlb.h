@@ -141,6 +141,23 @@ int lb_get_fields(lb_handle* h, double* rho1, double* rho2, double* T, double* u
 int lb_get_state(lb_handle* h, double* host, size_t bytes);
 int lb_set_state(lb_handle* h, const double* host, size_t bytes);
 
+/* Total shear stress of the current state: the stress of the rheology experiment (Sec. 2.1, text
+ * after Eq. NS: the bare viscous stress supplemented by the pressure tensor; Sec. 3.2.1: its space and
+ * time average is the stress Sigma of the flow curve, its x-wise average the Pxy_av profile).  At every
+ * fluid node
+ *   sigma_xy = eta_0 (d_x u^(H)_y + d_y u^(H)_x) - P^int_xy - P^F_xy,  eta_0 = rho (tau - 1/2) / 3 (Eq. VISCO),
+ * with central differences (a solid neighbour takes the mirror value 2 u_w - u: u_w = u_wall along x for
+ * a flat wall row, 0 otherwise), P^int_xy the virial form of the interaction forces of Eqs. FAB,
+ * FintAttrattive, FintRepulsive (half of every pair term times c_ix c_iy) and
+ * P^F_xy = tau^2 sum_l F_lx F_ly / rho_l - F_x F_y / (4 rho) the momentum flux of the forcing of Eq. shift
+ * (F_l the total force on component l).  In a steady shear the space-time average of sigma_xy balances
+ * the wall stress (wall_fx of lb_obs).  All arithmetic in FP64 from the fields of lb_get_fields.
+ * out4 (host, 4 doubles or NULL): means over the fluid nodes of sigma_xy, of the viscous part, of
+ * P^int_xy and of P^F_xy.  row (host, ny doubles or NULL): per row, the mean of sigma_xy over the row's
+ * fluid nodes (0 for a row without any).  field (host, nx*ny doubles or NULL): sigma_xy, 0 at solid
+ * nodes.  Uses the inactive buffer as staging; synchronous.  LB_EINVAL when all three are NULL. */
+int lb_stress(lb_handle* h, double* out4, double* row, double* field);
+
 /* Tile-shape autotuner of the fused step (not in the paper).  Times every step-kernel tile
  * candidate of the handle's precision over `launches` launches on the handle's stream and keeps the
  * fastest for later lb_step calls.  Each trial reads the current state and writes the inactive
@@ -265,6 +282,9 @@ int lb_batch_info(const lb_batch* b, int* n_items, int* grid, int* schedule, int
 int lb_batch_observables(lb_batch* b, int replica, lb_obs* out);
 int lb_batch_get_fields(lb_batch* b, int replica, double* rho1, double* rho2, double* T, double* ux, double* uy);
 int lb_batch_get_state(lb_batch* b, int replica, double* host, size_t bytes);
+
+/* Total shear stress of replica r, as lb_stress. */
+int lb_batch_stress(lb_batch* b, int replica, double* out4, double* row, double* field);
 
 /* Wait for the batch's stream; LB_ETIMEOUT if a persistent wait ran out. */
 int lb_batch_sync(lb_batch* b);

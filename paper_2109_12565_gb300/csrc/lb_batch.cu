@@ -628,6 +628,20 @@ int lb_batch_get_fields(lb_batch* b, int r, double* rho1, double* rho2, double* 
   return LB_OK;
 }
 
+int lb_batch_stress(lb_batch* b, int r, double* out4, double* row, double* field) {
+  if (!b || r < 0 || r >= b->n) return bfail(b, LB_EINVAL, "batch and replica are required");
+  if (!out4 && !row && !field) return bfail(b, LB_EINVAL, "lb_batch_stress: no output requested");
+  if (int rc = check_err_word(b)) return rc;
+  unsigned char* rb = b->ws + b->base[r];
+  const Layout& L = b->L[r];
+  void* cur = rb + (b->parity ? L.buf_bytes : 0);
+  double* stage = reinterpret_cast<double*>(rb + (b->parity ? 0 : L.buf_bytes));
+  double *d_rows = nullptr, *d_tot = nullptr;
+  BCUDA(b, stress_run(b->cfg[r], b->precision, cur, stage, b->stream, &d_rows, &d_tot));
+  BCUDA(b, stress_fetch(b->p[r].nx, b->p[r].ny, stage, d_rows, d_tot, out4, row, field, b->stream));
+  return LB_OK;
+}
+
 int lb_batch_get_state(lb_batch* b, int r, double* host, size_t bytes) {
   if (!b || !host || r < 0 || r >= b->n) return bfail(b, LB_EINVAL, "batch, replica and host buffer are required");
   const size_t N = (size_t)b->p[r].nx * b->p[r].ny;

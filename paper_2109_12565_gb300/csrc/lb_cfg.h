@@ -7,7 +7,11 @@
 
 namespace tlb {
 
-enum Mode : int { MODE_STEP = 0, MODE_OBS = 1, MODE_FIELDS = 2 };
+// MODE_STEP_NU: a step that also sums u^(H)_y T over the fluid nodes of its input state, one partial
+// per CTA (the Nusselt number's advective part, Eq. NuTime), for the adjoint's forward pass.
+enum Mode : int { MODE_STEP = 0, MODE_OBS = 1, MODE_FIELDS = 2, MODE_STEP_NU = 3 };
+__host__ __device__ constexpr bool mode_needs_T(int m) { return m == MODE_OBS || m == MODE_FIELDS; }
+__host__ __device__ constexpr bool mode_steps(int m) { return m == MODE_STEP || m == MODE_STEP_NU; }
 
 // Number of doubles each block writes to the partial-sum buffer in MODE_OBS.
 constexpr int kObsSlots = 12;
@@ -79,16 +83,24 @@ cudaError_t launch_step_tile_f32(int k, const StepCfg& c, const void* fin, void*
 cudaError_t launch_step_tile_f32h(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
 // Error codes a kernel writes to StepCfg::err (the host maps them to LB_ETIMEOUT).
 constexpr int kErrWaitTimeout = 1;
-// TMA-fed FP32 step (lb_tma.cu): candidates for the FP32 tile autotuner; they need StepCfg::err and
-// a lattice whose buffers are 16-byte aligned (always true for the workspace layout).
-int tma_count_f32();
-TileChoice tma_info_f32(int k);
-cudaError_t launch_step_tma_f32(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
-// Strip-marching TMA-fed FP32 step (lb_stream.cu): autotuner candidates after the TMA tile ones; they
-// need StepCfg::err, walls in y (periodic_y = 0) and nx >= 128, ny >= 8.
-int stream_count_f32();
-TileChoice stream_info_f32(int k);
-cudaError_t launch_step_stream_f32(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
+// Total shear stress (lb_stress.cu): the field mode writes rho_1, rho_2, T, u^(H) (5 planes of nx*ny
+// doubles) to `stage`, then sigma_xy (1 plane), per-row partials, row sums and totals follow there;
+// stress_staging_doubles is the staging it needs.  stress_fetch copies the means (out4), the per-row
+// means (row, ny) and sigma_xy (field, nx*ny) to the host; each may be nullptr.  Synchronous.
+constexpr int kStressTileX = 32, kStressRowVals = 5;
+inline size_t stress_staging_doubles(int nx, int ny) {
+  const size_t N = (size_t)nx * ny, ncol = (size_t)((nx + kStressTileX - 1) / kStressTileX);
+  return 6 * N + (ncol * ny + ny + 1) * kStressRowVals;
+}
+cudaError_t stress_run(const StepCfg& cfg, int precision, const void* cur, double* stage, cudaStream_t s,
+                       double** d_rows, double** d_tot);
+cudaError_t stress_fetch(int nx, int ny, const double* stage, const double* d_rows, const double* d_tot, double* out4,
+                         double* row, double* field, cudaStream_t s);
+// A step (MODE_STEP_NU) from fin to fout that also writes, per CTA, the sum of u^(H)_y T over the fluid
+// nodes of fin (step_nu_blocks partials, in CTA order); one fixed tile shape per precision.
+int step_nu_blocks(int precision, int nx, int ny);
+cudaError_t launch_step_nu_f64(const StepCfg& c, const void* fin, void* fout, double* partials, cudaStream_t s);
+cudaError_t launch_step_nu_f32(const StepCfg& c, const void* fin, void* fout, double* partials, cudaStream_t s);
 // Deterministic final reduction of n_blocks partials into kObsOut doubles.
 cudaError_t obs_finalize(const StepCfg& c, const double* partials, int n_blocks, double* out, cudaStream_t s);
 

@@ -57,8 +57,8 @@ inline Layout layout_for(const lb_params* p, int has_mask) {
   const size_t plane = (size_t)L.pitch * p->ny;
   // LB_FP32_FP16T: 18 FP32 fluid planes, then 9 FP16 thermal planes of the same pitch
   L.buf_bytes = round_up(p->precision == LB_FP32_FP16T ? (18 * 4 + 9 * 2) * plane : 27 * plane * L.elem, kAlign);
-  // the inactive buffer doubles as staging for init (3 planes) and fields (5 planes) of doubles
-  const size_t staging = (size_t)p->nx * p->ny * 5 * sizeof(double);
+  // the inactive buffer doubles as staging for init (3 planes), fields (5 planes) and the stress pass
+  const size_t staging = stress_staging_doubles(p->nx, p->ny) * sizeof(double);
   if (staging > L.buf_bytes) L.buf_bytes = round_up(staging, kAlign);
   size_t off = 2 * L.buf_bytes;
   L.mask_off = off;

@@ -26,7 +26,7 @@ EXPORTS = ("lb_workspace_size", "lb_init", "lb_step", "lb_observables", "lb_get_
            "lb_batch_sync", "lb_batch_set_wait_budget", "lb_batch_destroy", "lb_batch_last_error",
            "lb_state_layout", "lb_adjoint_workspace_size", "lb_adjoint_step", "lb_adjoint", "lb_adjoint_timing",
            "lb_droplets_workspace_size", "lb_droplets", "lb_droplets_get", "lb_droplets_nusselt",
-           "lb_droplets_compare")
+           "lb_droplets_compare", "lb_stress", "lb_batch_stress")
 
 
 class LbError(RuntimeError):
@@ -118,8 +118,12 @@ def lib():
                                           ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), i]
         L.lb_droplets_nusselt.argtypes = [vp, vp, sz, dp]
         for f in ("lb_droplets_workspace_size", "lb_droplets", "lb_droplets_get", "lb_droplets_nusselt",
-                  "lb_droplets_compare"):
+                  "lb_droplets_compare", "lb_stress", "lb_batch_stress"):
             getattr(L, f).restype = ctypes.c_int
+        L.lb_stress.argtypes = [vp, dp, dp, dp]
+        L.lb_stress.restype = ctypes.c_int
+        L.lb_batch_stress.argtypes = [vp, i, dp, dp, dp]
+        L.lb_batch_stress.restype = ctypes.c_int
         L.lb_version.argtypes = []
         L.lb_version.restype = ctypes.c_char_p
         for f in ("lb_workspace_size", "lb_init", "lb_step", "lb_observables", "lb_get_fields", "lb_get_state",
@@ -226,6 +230,15 @@ class Lattice:
         st = np.zeros((27, self.ny, self.nx))
         _check(lib().lb_get_state(self._h, _dp(st), st.nbytes), self._h)
         return st
+
+    def stress(self, field=True):
+        """Total shear stress (lb_stress): means of sigma_xy ("Sigma"), of its viscous part ("visc"), of
+        the interaction pressure tensor ("pint") and of the forcing part ("pforce"), the per-row means
+        "row" [ny] and, with field=True, sigma_xy "sxy" [ny, nx]."""
+        out, row = np.zeros(4), np.zeros(self.ny)
+        f = np.zeros((self.ny, self.nx)) if field else None
+        _check(lib().lb_stress(self._h, _dp(out), _dp(row), _dp(f)), self._h)
+        return {"Sigma": out[0], "visc": out[1], "pint": out[2], "pforce": out[3], "row": row, "sxy": f}
 
     def set_state(self, state):
         st = np.ascontiguousarray(state, dtype=np.float64)
@@ -499,6 +512,14 @@ class Batch:
         st = np.zeros((27, ny, nx))
         _bcheck(lib().lb_batch_get_state(self._b, int(r), _dp(st), st.nbytes), self._b)
         return st
+
+    def stress(self, r, field=True):
+        """lb_batch_stress of replica r (see Lattice.stress)."""
+        ny, nx = self.shapes[r]
+        out, row = np.zeros(4), np.zeros(ny)
+        f = np.zeros((ny, nx)) if field else None
+        _bcheck(lib().lb_batch_stress(self._b, int(r), _dp(out), _dp(row), _dp(f)), self._b)
+        return {"Sigma": out[0], "visc": out[1], "pint": out[2], "pforce": out[3], "row": row, "sxy": f}
 
     def sync(self):
         return lib().lb_batch_sync(self._b)
