@@ -349,6 +349,20 @@ __global__ void lb_adj_dT0_kernel(const S* __restrict__ lam, double* __restrict_
 
 // J = mean of Nu over the N post-step observables; dJ/dT_down = sum of the per-block totals
 // - J / dT (Nu depends on T_down through the normalisation kappa dT / H).
+// Nu(S_t) of Eq. NuTime for the forward steps t = 1 .. n - 1 from the u^(H)_y T partials of the step out
+// of S_t (nb per step, summed in CTA order): Nu = nuc (U - kappa D) with D the mirror-rule sum of dT/dy,
+// which telescopes to the wall temperatures (the same for every state).  Slot t - 1 of nu, as the
+// observables pass would fill it.
+__global__ void lb_adj_nu_kernel(const double* __restrict__ part, int nb, int n, double nuc, double mirror_D,
+                                 double* __restrict__ nu) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  if (t >= n) return;
+  const double* p = part + (long long)t * nb;
+  double U = 0.0;
+  for (int b = 0; b < nb; ++b) U += p[b];
+  nu[(long long)(t - 1) * kObsOut + 4] = nuc * U + mirror_D;
+}
+
 __global__ void lb_adj_final_kernel(const double* __restrict__ nu, int n_steps, const double* __restrict__ acc,
                                     int n_blocks, double inv_dT, double* __restrict__ out) {
   __shared__ double s_a[256], s_b[256];
@@ -403,8 +417,8 @@ cudaError_t adj_step_impl(const StepCfg& c, const void* S_t, const void* lam_out
 namespace {
 
 struct AdjLayout {
-  size_t state = 0, lam = 0, lamF = 0, acc = 0, nu = 0, red = 0, dT0 = 0, ckpt = 0, seg = 0, total = 0;
-  int n_ckpt = 0, n_blocks = 0;
+  size_t state = 0, lam = 0, lamF = 0, acc = 0, nu = 0, nup = 0, red = 0, dT0 = 0, ckpt = 0, seg = 0, total = 0;
+  int n_ckpt = 0, n_blocks = 0, nu_blocks = 0;
 };
 
 int adj_blocks(const lb_params& p) {
@@ -431,6 +445,9 @@ AdjLayout adj_layout(const lb_handle* h, int n_steps, int ckpt_every) {
   off += kAlign;
   A.nu = off;
   off += round_up((size_t)(n_steps + 1) * kObsOut * sizeof(double), kAlign);
+  A.nu_blocks = step_nu_blocks(h->p.precision, h->p.nx, h->p.ny);
+  A.nup = off;  // per forward step: the u^(H)_y T partial sums of its input state, one per CTA
+  off += round_up((size_t)n_steps * A.nu_blocks * sizeof(double), kAlign);
   A.dT0 = off;
   off += round_up((size_t)h->p.nx * h->p.ny * sizeof(double), kAlign);
   A.ckpt = off;
@@ -481,6 +498,11 @@ cudaError_t fwd_step(const lb_handle* h, const void* in, void* out) {
                                    : launch_step_tile_f32(h->tile, h->cfg, in, out, h->stream);
 }
 
+cudaError_t fwd_step_nu(const lb_handle* h, const void* in, void* out, double* partials) {
+  return h->p.precision == LB_FP64 ? launch_step_nu_f64(h->cfg, in, out, partials, h->stream)
+                                   : launch_step_nu_f32(h->cfg, in, out, partials, h->stream);
+}
+
 cudaError_t obs_into(const lb_handle* h, const void* state, double* out16) {
   double* part = reinterpret_cast<double*>(h->ws + h->L.part_off);
   cudaError_t e = h->p.precision == LB_FP64 ? launch_f64(MODE_OBS, h->cfg, state, nullptr, part, h->stream)
@@ -491,13 +513,14 @@ cudaError_t obs_into(const lb_handle* h, const void* state, double* out16) {
 
 // d Nu / d(sum u_y T) = 1 / (N_fluid kappa dT / H), and the coefficient of the mirror count
 // (-kappa times that); both 0 when Nu is not defined (periodic y or dT = 0).
-int nu_coefs(lb_handle* h, const void* state, double* scratch16, double* nuc, double* mirror) {
+int nu_coefs(lb_handle* h, const void* state, double* scratch16, double* nuc, double* mirror, double* dsum = nullptr) {
   cudaError_t e = obs_into(h, state, scratch16);
   double v[kObsOut];
   if (e == cudaSuccess) e = cudaMemcpyAsync(v, scratch16, sizeof v, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return afail(h, LB_ECUDA, "observables for the adjoint", e);
   const double nf = v[7], dT = h->p.T_down - h->p.T_up, kappa = h->cfg.kappa;
+  if (dsum) *dsum = v[9];
   if (h->p.periodic_y || dT == 0.0 || nf <= 0.0) {
     *nuc = *mirror = 0.0;
   } else {
@@ -571,21 +594,27 @@ int lb_adjoint(lb_handle* h, int n_steps, int ckpt_every, void* d_adj_ws, size_t
   auto ckpt = [&](int k) { return ws + A.ckpt + (size_t)k * A.state; };
   auto seg = [&](int j) { return ws + A.seg + (size_t)j * A.state; };
   const size_t sbytes = (size_t)27 * h->L.pitch * h->p.ny * h->L.elem;
-  double nuc = 0.0, mirror = 0.0;
-  if (int rc = nu_coefs(h, h->buf[h->cur], red, &nuc, &mirror)) return rc;
+  double nuc = 0.0, mirror = 0.0, dsum = 0.0;
+  if (int rc = nu_coefs(h, h->buf[h->cur], red, &nuc, &mirror, &dsum)) return rc;
   cudaStream_t s = h->stream;
+  double* nup = reinterpret_cast<double*>(ws + A.nup);
   EventPair t_fwd;
   std::vector<EventPair> t_rec(A.n_ckpt), t_rev(A.n_ckpt);
-  // forward pass: Nu after every step, a checkpoint every ckpt_every steps
+  // forward pass, a checkpoint every ckpt_every steps: each step also sums u^(H)_y T of its input state,
+  // which gives Nu(S_1) .. Nu(S_{n-1}); Nu(S_n) comes from one observables pass at the end
   cudaEventRecord(t_fwd.a, s);
   cudaError_t e = cudaMemcpyAsync(ckpt(0), h->buf[h->cur], sbytes, cudaMemcpyDeviceToDevice, s);
   for (int t = 0; t < n_steps && e == cudaSuccess; ++t) {
-    e = fwd_step(h, h->buf[h->cur], h->buf[h->cur ^ 1]);
+    e = fwd_step_nu(h, h->buf[h->cur], h->buf[h->cur ^ 1], nup + (size_t)t * A.nu_blocks);
     h->cur ^= 1;
     h->step += 1;
-    if (e == cudaSuccess) e = obs_into(h, h->buf[h->cur], nu + (size_t)t * kObsOut);
     if (e == cudaSuccess && (t + 1) % ckpt_every == 0 && t + 1 < n_steps)
       e = cudaMemcpyAsync(ckpt((t + 1) / ckpt_every), h->buf[h->cur], sbytes, cudaMemcpyDeviceToDevice, s);
+  }
+  if (e == cudaSuccess) e = obs_into(h, h->buf[h->cur], nu + (size_t)(n_steps - 1) * kObsOut);
+  if (e == cudaSuccess && n_steps > 1) {
+    lb_adj_nu_kernel<<<(n_steps + 127) / 128, 128, 0, s>>>(nup, A.nu_blocks, n_steps, nuc, mirror * dsum, nu);
+    e = cudaGetLastError();
   }
   cudaEventRecord(t_fwd.b, s);
   if (e != cudaSuccess) return afail(h, LB_ECUDA, "adjoint forward pass", e);

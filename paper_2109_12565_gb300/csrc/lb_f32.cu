@@ -32,24 +32,19 @@ const Cand kCands[] = {
 };
 }  // namespace
 
-constexpr int kPlain = (int)(sizeof kCands / sizeof kCands[0]);
-
-// Candidates 0 .. kPlain-1: the plain tile kernel; then the TMA-fed pipelined tile kernel (lb_tma.cu);
-// then the strip-marching kernel (lb_stream.cu).  A candidate that does not apply to the lattice runs
-// candidate 0 instead.
-int tile_count_f32() { return kPlain + tma_count_f32() + stream_count_f32(); }
-TileChoice tile_info_f32(int k) {
-  if (k < kPlain) return kCands[k].t;
-  k -= kPlain;
-  if (k < tma_count_f32()) return tma_info_f32(k);
-  return stream_info_f32(k - tma_count_f32());
-}
+int tile_count_f32() { return (int)(sizeof kCands / sizeof kCands[0]); }
+TileChoice tile_info_f32(int k) { return kCands[k].t; }
 cudaError_t launch_step_tile_f32(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s) {
-  if (k < kPlain) return kCands[k].fn(c, fin, fout, s);
-  k -= kPlain;
-  const cudaError_t e = k < tma_count_f32() ? launch_step_tma_f32(k, c, fin, fout, s)
-                                            : launch_step_stream_f32(k - tma_count_f32(), c, fin, fout, s);
-  return e == cudaErrorNotSupported ? kCands[0].fn(c, fin, fout, s) : e;
+  return kCands[k].fn(c, fin, fout, s);
+}
+
+// The adjoint's forward step with the u^(H)_y T partial sums: the 32 x 8 tile (one phase-A pass of node
+// pairs, one phase-B node per thread).
+cudaError_t launch_step_nu_f32(const StepCfg& c, const void* fin, void* fout, double* partials, cudaStream_t s) {
+  return launch_tile_kernel<float, MODE_STEP_NU, 32, 8, 8, 4, true>(grid_for(c.nx, c.ny, 32, 8),
+                                                                   static_cast<const float*>(fin),
+                                                                   static_cast<float*>(fout), make_kparams<float>(c),
+                                                                   partials, s);
 }
 
 cudaError_t init_f32(const StepCfg& c, const double* fields, void* buf, cudaStream_t s) {

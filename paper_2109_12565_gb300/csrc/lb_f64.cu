@@ -1,6 +1,7 @@
 // FP64 instantiation of the fused step (populations and arithmetic in FP64)
 // and the deterministic final reduction of the observables.
 #include "lb_kernels.cuh"
+#include "tlb.h"
 
 namespace tlb {
 
@@ -25,6 +26,19 @@ int tile_count_f64() { return (int)(sizeof kCands / sizeof kCands[0]); }
 TileChoice tile_info_f64(int k) { return kCands[k].t; }
 cudaError_t launch_step_tile_f64(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s) {
   return kCands[k].fn(c, fin, fout, s);
+}
+
+// The adjoint's forward step with the u^(H)_y T partial sums: the shape of tile candidate 0.
+cudaError_t launch_step_nu_f64(const StepCfg& c, const void* fin, void* fout, double* partials, cudaStream_t s) {
+  return launch_tile_kernel<double, MODE_STEP_NU, 32, 16, 8, 2, false>(grid_for(c.nx, c.ny, 32, 16),
+                                                                      static_cast<const double*>(fin),
+                                                                      static_cast<double*>(fout), make_kparams<double>(c),
+                                                                      partials, s);
+}
+
+int step_nu_blocks(int precision, int nx, int ny) {
+  const dim3 g = precision == LB_FP64 ? grid_for(nx, ny, 32, 16) : grid_for(nx, ny, 32, 8);
+  return (int)(g.x * g.y);
 }
 
 cudaError_t init_f64(const StepCfg& c, const double* fields, void* buf, cudaStream_t s) {

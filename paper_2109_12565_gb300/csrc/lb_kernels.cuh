@@ -762,11 +762,11 @@ __device__ __forceinline__ NodeMoments<C> node_moments(const SMT& sm, const KPar
 
 // The rest of a fluid node's step once its moments and interaction forces (Fx, and Fyp without the
 // buoyancy) are known: buoyancy, velocities (Eq. velo, Eq. shift, u^(H) = u + F / (2 rho)), BGK
-// collisions and the push store.
+// collisions and the push store.  Returns u^(H)_y T (the advective part of Eq. NuTime).
 template <class S, class C, bool SHIFT, bool FAST, class SMT>
-__device__ __forceinline__ void step_finish(SF<S>* __restrict__ fout, const KParams<C>& kp, const SMT& sm,
-                                            const C f[9], const C h[9], const C g[9], const NodeMoments<C>& m,
-                                            int tx, int ty, int gx, int gy, int idx, V2<C> Fx2, V2<C> Fyp) {
+__device__ __forceinline__ C step_finish(SF<S>* __restrict__ fout, const KParams<C>& kp, const SMT& sm,
+                                         const C f[9], const C h[9], const C g[9], const NodeMoments<C>& m,
+                                         int tx, int ty, int gx, int gy, int idx, V2<C> Fx2, V2<C> Fyp) {
   const V2<C> Fy2 = buoyant_fy<C>(kp, Fyp, v2<C>(m.r1, m.r2), m.T);
   const C Fx[2] = {Fx2.x, Fx2.y}, Fy[2] = {Fy2.x, Fy2.y};
   C i1, i2, inv_rho, ux, uy, uHx, uHy;
@@ -775,13 +775,14 @@ __device__ __forceinline__ void step_finish(SF<S>* __restrict__ fout, const KPar
   C post[27];
   node_collide<C, SHIFT>(kp, f, h, g, m.r1, m.r2, m.dr1, m.dr2, m.T, m.dT, ux, uy, i1, i2, Fx, Fy, uHx, uHy, post);
   push_store<S, C, FAST>(fout, kp, idx, gx, gy, post, sm.solid, tx + 2, ty + 2, m.r1, m.r2);
+  return uHy * m.T;
 }
 
 // Phase B on one tile.  MODE_STEP: collide and push-store; MODE_OBS: accumulate the observables
 // of the node into acc[]; MODE_FIELDS: write rho1, rho2, T, u^(H) to aux planes.
 template <class S, class C, bool SHIFT, int MODE, bool FAST, int TX, int TY, int BY, class Src>
 __device__ __forceinline__ void tile_phase_b(const Src& pop, SF<S>* __restrict__ fout, const KParams<C>& kp, int x0, int y0,
-                                             const TileSmem<C, TX, TY, MODE != MODE_STEP>& sm, double* __restrict__ aux,
+                                             const TileSmem<C, TX, TY, mode_needs_T(MODE)>& sm, double* __restrict__ aux,
                                              double acc[kObsSlots]) {
   const int nx = kp.nx, ny = kp.ny, pitch = kp.pitch, plane = kp.plane;
 #pragma unroll 1
@@ -819,8 +820,9 @@ __device__ __forceinline__ void tile_phase_b(const Src& pop, SF<S>* __restrict__
     const C dr1 = m.dr1, dr2 = m.dr2, r1 = m.r1, r2 = m.r2, dT = m.dT, T = m.T;
     V2<C> fx2, fyp2, q0, q1, q2, q3, q4;
     node_force_pair<C>(sm, kp, cx, cy, v2<C>(r1, r2), fx2, fyp2, q0, q1, q2, q3, q4);
-    if constexpr (MODE == MODE_STEP) {
-      step_finish<S, C, SHIFT, FAST>(fout, kp, sm, f, h, g, m, tx, ty, gx, gy, idx, fx2, fyp2);
+    if constexpr (mode_steps(MODE)) {
+      const C uyT = step_finish<S, C, SHIFT, FAST>(fout, kp, sm, f, h, g, m, tx, ty, gx, gy, idx, fx2, fyp2);
+      if constexpr (MODE == MODE_STEP_NU) acc[0] += (double)uyT;  // as MODE_OBS accumulates it
       continue;
     }
     const V2<C> fy2 = buoyant_fy<C>(kp, fyp2, v2<C>(r1, r2), T);
@@ -876,13 +878,13 @@ __device__ __forceinline__ void tile_phase_b(const Src& pop, SF<S>* __restrict__
 // One tile: phase A, barrier, phase B (fast path when the CTA allows it).
 template <class S, class C, bool SHIFT, int MODE, int TX, int TY, int BY, bool CG = false>
 __device__ __forceinline__ void tile_step(const SF<S>* __restrict__ fin, SF<S>* __restrict__ fout, const KParams<C>& kp,
-                                          int x0, int y0, TileSmem<C, TX, TY, MODE != MODE_STEP>& sm,
+                                          int x0, int y0, TileSmem<C, TX, TY, mode_needs_T(MODE)>& sm,
                                           double* __restrict__ aux, double acc[kObsSlots]) {
   constexpr int NT = TX * BY;
   const int tid = threadIdx.y * TX + threadIdx.x;
-  const bool fast = tile_phase_a<S, C, SHIFT, MODE != MODE_STEP, TX, TY, NT, CG>(fin, kp, x0, y0, sm, tid);
+  const bool fast = tile_phase_a<S, C, SHIFT, mode_needs_T(MODE), TX, TY, NT, CG>(fin, kp, x0, y0, sm, tid);
   const GlobalPopSource<S, CG> pop{fin, kp.plane};
-  if (MODE == MODE_STEP && fast)
+  if (mode_steps(MODE) && fast)
     tile_phase_b<S, C, SHIFT, MODE, true, TX, TY, BY>(pop, fout, kp, x0, y0, sm, aux, acc);
   else
     tile_phase_b<S, C, SHIFT, MODE, false, TX, TY, BY>(pop, fout, kp, x0, y0, sm, aux, acc);
@@ -907,16 +909,32 @@ __device__ __forceinline__ void block_obs_store(double acc[kObsSlots], double* _
   }
 }
 
+// Block-wide deterministic sum of one value per thread into aux[slot].
+template <int NT>
+__device__ __forceinline__ void block_sum_store(double v, double* __restrict__ aux, long long slot) {
+  __shared__ double s_red1[NT / 32];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const double s = warp_sum(v);
+  if ((tid & 31) == 0) s_red1[tid >> 5] = s;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += s_red1[w];
+    aux[slot] = t;
+  }
+}
+
 template <class S, class C, bool SHIFT, int MODE, int TX, int TY, int BY, int MINB>
 __global__ void __launch_bounds__(TX * BY, MINB)
 lb_step_kernel(const SF<S>* __restrict__ fin, SF<S>* __restrict__ fout, const KParams<C> kp, double* __restrict__ aux) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  auto& sm = *reinterpret_cast<TileSmem<C, TX, TY, MODE != MODE_STEP>*>(smem_raw);
+  auto& sm = *reinterpret_cast<TileSmem<C, TX, TY, mode_needs_T(MODE)>*>(smem_raw);
   double acc[kObsSlots];
 #pragma unroll
   for (int v = 0; v < kObsSlots; ++v) acc[v] = 0.0;
   tile_step<S, C, SHIFT, MODE, TX, TY, BY>(fin, fout, kp, blockIdx.x * TX, blockIdx.y * TY, sm, aux, acc);
   if constexpr (MODE == MODE_OBS) block_obs_store<TX * BY>(acc, aux, (long long)blockIdx.y * gridDim.x + blockIdx.x);
+  if constexpr (MODE == MODE_STEP_NU) block_sum_store<TX * BY>(acc[0], aux, (long long)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // Rest equilibria f = w_i rho, g = w_i T at fluid nodes (stored minus the shift), 0 at solid nodes.
@@ -982,7 +1000,7 @@ __global__ void lb_plane_put_kernel(int k, const double* __restrict__ in, SF<S>*
 template <class S, int MODE, int TX, int TY, int BY, int MB, bool SHIFT>
 cudaError_t launch_tile_kernel(const dim3& grid, const SF<S>* in, SF<S>* out, const KParams<SC<S>>& kp, double* aux,
                                cudaStream_t s) {
-  constexpr size_t bytes = sizeof(TileSmem<SC<S>, TX, TY, MODE != MODE_STEP>);
+  constexpr size_t bytes = sizeof(TileSmem<SC<S>, TX, TY, mode_needs_T(MODE)>);
   auto kern = lb_step_kernel<S, SC<S>, SHIFT, MODE, TX, TY, BY, MB>;
   static std::atomic<unsigned long long> done{0};  // one bit per device ordinal (mod 64)
   int dev = 0;
