@@ -335,10 +335,9 @@ def test_init_errors():
 @pytest.mark.parametrize("periodic", [0, 1])
 @pytest.mark.parametrize("nx,ny", [(300, 130), (277, 45)])
 def test_every_tile_candidate_gives_identical_results(precision, periodic, nx, ny):
-    """Tile shapes (and, in FP32, the TMA-fed pipelined kernels) only change which CTA computes a node
-    and how its populations reach shared memory, never the arithmetic of a node: every autotuner
-    candidate must give bit-identical populations (fast interior path, general path, ragged tiles,
-    periodic wrap)."""
+    """Tile shapes only change which CTA computes a node and how its inputs reach shared memory, never
+    the arithmetic of a node: every autotuner candidate must give bit-identical populations (fast
+    interior path, general path, ragged and odd-width tiles, periodic wrap)."""
     if periodic:
         y, x = np.mgrid[0:ny, 0:nx]
         r1 = np.where(((x - nx // 2) ** 2 + (y - ny // 2) ** 2) < (ny // 3) ** 2, 1.4, 0.1)
