@@ -9,7 +9,10 @@
 //   1  persistent: one cooperative launch of co-resident CTAs runs K steps;
 //      CTA b owns items b, b + G, b + 2G, ... and processes them in step
 //      order.  Each item publishes "steps done" in a counter (st.release);
-//      before step s an item waits (ld.acquire, bounded by a clock budget)
+//      before step s an item waits (ld.acquire, bounded by a clock budget;
+//      eight lanes of the second warp watch the eight neighbours at once,
+//      while thread 0 publishes the previous item: a barrier, then one
+//      st.release, which is cumulative over the barrier)
 //      until its 8 neighbour tiles have done s steps, which orders every read
 //      of step s after the neighbours' writes of step s - 1 and every write of
 //      step s after their reads of step s - 1.  Loads bypass L1 (ld.global.cg)
@@ -77,35 +80,44 @@ lb_batch_persistent_kernel(const ReplicaDesc<S>* __restrict__ reps, const int4* 
     const int parity = (parity0 + s) & 1;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
       const int4 it = items[item];
-      if (tid == 0) {
-        int ok = ld_relaxed_gpu(err) == 0;
+      if (tid >= 32 && tid < 64) {
+        // warp 1: lanes 0-7 each watch one neighbour's counter, so one round trip covers all eight;
+        // meanwhile thread 0 (warp 0) may still be publishing the previous item
+        const int lane = tid - 32;
+        int ok = lane == 0 ? (ld_relaxed_gpu(err) == 0) : 1;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
         if (ok && s > 0) {
+          const int nb = lane < 8 ? nbrs[item * 8 + lane] : -1;
+          bool ready = nb < 0;
           const long long t0 = clock64();
-          for (int k = 0; k < 8 && ok; ++k) {
-            const int nb = nbrs[item * 8 + k];
-            if (nb < 0) continue;
-            while (ld_acquire_gpu(counters + nb) < s) {
+          for (;;) {
+            if (!ready) ready = ld_acquire_gpu(counters + nb) >= s;
+            if (__all_sync(0xffffffffu, ready)) break;
+            int stop = 0;
+            if (lane == 0) {
               if (ld_relaxed_gpu(err) != 0) {
-                ok = 0;
-                break;
-              }
-              if (clock64() - t0 > budget) {
+                stop = 1;
+              } else if (clock64() - t0 > budget) {
                 atomicCAS(err, 0, 1);
-                ok = 0;
-                break;
+                stop = 1;
               }
-              __nanosleep(64);
             }
+            if (__shfl_sync(0xffffffffu, stop, 0)) {
+              ok = 0;
+              break;
+            }
+            __nanosleep(64);
           }
         }
-        s_go = ok;
+        if (lane == 0) s_go = ok;
       }
       __syncthreads();
       if (!s_go) return;
       const ReplicaDesc<S>& rd = reps[it.x];
       tile_step<S, S, SHIFT, MODE_STEP, TX, TY, BY, true>(rd.buf[parity], rd.buf[parity ^ 1], rd.kp, it.y, it.z, sm,
                                                           nullptr, acc);
-      __threadfence();
+      // every thread's stores of this item come before the barrier; the release by thread 0 is cumulative
+      // over it, so a neighbour that acquires the counter sees all of them
       __syncthreads();
       if (tid == 0 && item != withhold) st_release_gpu(counters + item, s + 1);
     }
