@@ -432,8 +432,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="fp32,fp64,fp16t,batched,adjoint,rough,droplets",
-                    help="comma list of fp32, fp64, fp16t, batched, adjoint, rough, droplets")
+    ap.add_argument("--forms", default="fp32,fp64,df64,fp16t,batched,adjoint,rough,droplets",
+                    help="comma list of fp32, fp64, df64, fp16t, batched, adjoint, rough, droplets")
     ap.add_argument("--rough-steps", type=int, default=200, help="timed steps of the 4096 x 2048 rough channel")
     ap.add_argument("--fp64-steps", type=int, default=0, help="timed FP64 steps (default steps // 4)")
     ap.add_argument("--tile", type=int, default=-1,
@@ -480,6 +480,7 @@ def main():
             r32 = time_form(w, lb.LB_FP32_SHIFTED, args.steps, args.warmup, flush, args.tile)
         if "fp64" in forms_req:
             r64 = time_form(w, lb.LB_FP64, steps64, args.warmup, flush, args.tile)
+        rdf = time_form(w, lb.LB_DF64, steps64, args.warmup, flush, args.tile) if "df64" in forms_req else None
         r16 = time_form(w, lb.LB_FP32_FP16T, args.steps, args.warmup, flush, args.tile) if "fp16t" in forms_req else None
         rb = time_batch(ens, args.batch_steps, args.warmup) if ens else None
         wr = I.rough_channel_4096x2048() if "rough" in forms_req else None
@@ -493,9 +494,10 @@ def main():
     torch.cuda.synchronize()
     e2e = time_e2e(w, lb.LB_FP32_SHIFTED, args.e2e_steps) if args.e2e_steps > 0 else None
     # every rank's timed totals, max over ranks, before rank 0 alone goes on to report
-    t32, t64, t16, trr, tb, te2e = max_over_ranks(
+    t32, t64, t16, trr, tb, te2e, tdf = max_over_ranks(
         [r32["ms_total"] if r32 else 0.0, r64["ms_total"] if r64 else 0.0, r16["ms_total"] if r16 else 0.0,
-         rr["ms_total"] if rr else 0.0, rb["ms_total"] if rb else 0.0, e2e["seconds"] if e2e else 0.0],
+         rr["ms_total"] if rr else 0.0, rb["ms_total"] if rb else 0.0, e2e["seconds"] if e2e else 0.0,
+         rdf["ms_total"] if rdf else 0.0],
         dist, "cuda")
     mlups32 = aggregate_mlups(world, N, args.steps, t32) if r32 else None
     mlups64 = aggregate_mlups(world, N, steps64, t64) if r64 else None
@@ -556,6 +558,15 @@ def main():
         if step_ms:
             forms["droplets_ms"]["fp32_steps_1024x512"] = rdrop["emulsion_1024x512"]["ms"] / step_ms
         detail["droplets"] = rdrop
+    if rdf:
+        # double-float storage and arithmetic on the FP32 pipe, held to the FP64 tolerance of the oracle
+        achdf = bytes64 / (rdf["ms_per_step"] * 1e-3) / 1e9
+        forms["df64"] = {"MLUPS": aggregate_mlups(world, N, steps64, tdf), "ms_per_step": rdf["ms_per_step"],
+                         "hbm_frac": achdf / peak, "bytes_per_update": 432, "Nu": rdf["obs"]["Nu"],
+                         "tile": tile_of(rdf)}
+        if r64:
+            forms["df64"]["over_fp64"] = forms["df64"]["MLUPS"] / mlups64
+        detail["df64_autotune_ms_per_candidate"] = rdf["autotune_ms_per_candidate"]
     if r64:
         # the paper's arithmetic: FP64 storage and FP64 arithmetic; bound by the FP64 pipe, not by HBM
         ach64 = bytes64 / (r64["ms_per_step"] * 1e-3) / 1e9
@@ -589,7 +600,8 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": (args.steps if r32 else 0) + (steps64 if r64 else 0) + (args.steps if r16 else 0) + (
+        "gpu_launches": (args.steps if r32 else 0) + (steps64 if r64 else 0) + (steps64 if rdf else 0) + (
+            args.steps if r16 else 0) + (
             args.rough_steps if rr else 0) + (
             (args.batch_steps if rb["info"]["schedule"] == 0 else -(-args.batch_steps // 64)) if rb else 0),
         "clocks": clk.summary(),

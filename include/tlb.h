@@ -60,11 +60,17 @@ extern "C" {
                                FP16 (round to nearest on every store): 180 bytes of population traffic
                                per lattice update instead of 216 (not in the paper).  Single lattices
                                only: lb_batch_* and lb_adjoint* return LB_EINVAL for it. */
+#define LB_DF64 3           /* populations stored as double-float pairs (hi, lo) of FP32 numbers, 8 bytes each (the
+                               FP64 footprint), every operation in double-float arithmetic on the FP32 pipe
+                               (error-free two-sum and two-product; a 48-bit significand); results within the
+                               FP64 form's tolerance of the FP64 oracle (not in the paper).  lb_get_state /
+                               lb_set_state convert to and from FP64.  Single lattices only: lb_batch_* and
+                               lb_adjoint* return LB_EINVAL for it. */
 
 typedef struct lb_params {
   int nx, ny;          /* lattice size including wall rows */
   int periodic_y;      /* 0: solid rows y = 0, ny-1; 1: periodic in y */
-  int precision;       /* LB_FP64, LB_FP32_SHIFTED or LB_FP32_FP16T */
+  int precision;       /* LB_FP64, LB_FP32_SHIFTED, LB_FP32_FP16T or LB_DF64 */
   double tau;          /* fluid relaxation time (> 1/2), Eq. BGK */
   double tau_g;        /* thermal relaxation time (> 1/2), Eq. LBMg */
   double rho0;         /* reference density of psi~ and psi (> 0) */

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtlbgb300.so")
-SOURCES = ["lb_api.cu", "lb_f64.cu", "lb_f32.cu", "lb_static.cu", "lb_batch.cu", "lb_adjoint.cu", "lb_f32h.cu", "lb_droplets.cu", "lb_stress.cu"]
+SOURCES = ["lb_api.cu", "lb_f64.cu", "lb_f32.cu", "lb_static.cu", "lb_batch.cu", "lb_adjoint.cu", "lb_f32h.cu", "lb_droplets.cu", "lb_stress.cu", "lb_df64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "128",
          "-I", CSRC, "-I", INCLUDE]

@@ -543,7 +543,8 @@ int lb_state_layout(const lb_handle* h, int* pitch, size_t* plane_elems, int* el
 }
 
 int lb_adjoint_workspace_size(const lb_handle* h, int n_steps, int ckpt_every, size_t* bytes) {
-  if (!h || !bytes || n_steps < 1 || ckpt_every < 1 || h->p.precision == LB_FP32_FP16T) return LB_EINVAL;
+  if (!h || !bytes || n_steps < 1 || ckpt_every < 1 || h->p.precision == LB_FP32_FP16T || h->p.precision == LB_DF64)
+    return LB_EINVAL;
   *bytes = adj_layout(h, n_steps, ckpt_every).total;
   return LB_OK;
 }
@@ -551,7 +552,8 @@ int lb_adjoint_workspace_size(const lb_handle* h, int n_steps, int ckpt_every, s
 int lb_adjoint_step(lb_handle* h, const void* d_lam_next, void* d_lam, double cJ, void* d_adj_ws, size_t adj_bytes,
                     double* dJ_dTdown) {
   if (!h || !d_lam || !d_adj_ws) return LB_EINVAL;
-  if (h->p.precision == LB_FP32_FP16T) return afail(h, LB_EINVAL, "the adjoint needs LB_FP64 or LB_FP32_SHIFTED");
+  if (h->p.precision == LB_FP32_FP16T || h->p.precision == LB_DF64)
+    return afail(h, LB_EINVAL, "the adjoint needs LB_FP64 or LB_FP32_SHIFTED");
   if (h->cfg.u_wall[0] != 0.0 || h->cfg.u_wall[1] != 0.0) return afail(h, LB_EINVAL, "the adjoint needs resting walls");
   const AdjLayout A = adj_layout(h, 1, 1);
   if (adj_bytes < A.total || ((uintptr_t)d_adj_ws % kAlign) != 0) return afail(h, LB_ENOSPACE, "adjoint workspace too small");
@@ -583,7 +585,8 @@ int lb_adjoint_step(lb_handle* h, const void* d_lam_next, void* d_lam, double cJ
 int lb_adjoint(lb_handle* h, int n_steps, int ckpt_every, void* d_adj_ws, size_t adj_bytes, double* J, double* dJ_dT0,
                double* dJ_dTdown) {
   if (!h || n_steps < 1 || ckpt_every < 1 || !d_adj_ws || !J) return LB_EINVAL;
-  if (h->p.precision == LB_FP32_FP16T) return afail(h, LB_EINVAL, "the adjoint needs LB_FP64 or LB_FP32_SHIFTED");
+  if (h->p.precision == LB_FP32_FP16T || h->p.precision == LB_DF64)
+    return afail(h, LB_EINVAL, "the adjoint needs LB_FP64 or LB_FP32_SHIFTED");
   if (h->cfg.u_wall[0] != 0.0 || h->cfg.u_wall[1] != 0.0) return afail(h, LB_EINVAL, "the adjoint needs resting walls");
   const AdjLayout A = adj_layout(h, n_steps, ckpt_every);
   if (adj_bytes < A.total || ((uintptr_t)d_adj_ws % kAlign) != 0) return afail(h, LB_ENOSPACE, "adjoint workspace too small");

@@ -46,44 +46,60 @@ int fail(lb_handle* h, int code, const char* fmt, ...) {
 
 cudaError_t launch(const lb_handle* h, int mode, const void* fin, void* fout, double* aux, cudaStream_t s) {
   const int pr = h->p.precision;
-  if (mode == MODE_STEP)
-    return pr == LB_FP64 ? launch_step_tile_f64(h->tile, h->cfg, fin, fout, s)
-                         : (pr == LB_FP32_SHIFTED ? launch_step_tile_f32(h->tile, h->cfg, fin, fout, s)
-                                                  : launch_step_tile_f32h(h->tile, h->cfg, fin, fout, s));
-  return pr == LB_FP64 ? launch_f64(mode, h->cfg, fin, fout, aux, s)
-                       : (pr == LB_FP32_SHIFTED ? launch_f32(mode, h->cfg, fin, fout, aux, s)
-                                                : launch_f32h(mode, h->cfg, fin, fout, aux, s));
+  if (mode == MODE_STEP) {
+    switch (pr) {
+      case LB_FP64: return launch_step_tile_f64(h->tile, h->cfg, fin, fout, s);
+      case LB_FP32_SHIFTED: return launch_step_tile_f32(h->tile, h->cfg, fin, fout, s);
+      case LB_FP32_FP16T: return launch_step_tile_f32h(h->tile, h->cfg, fin, fout, s);
+      default: return launch_step_tile_df64(h->tile, h->cfg, fin, fout, s);
+    }
+  }
+  return launch_mode(pr, mode, h->cfg, fin, fout, aux, s);
 }
 
 int tile_count(const lb_handle* h) {
-  const int pr = h->p.precision;
-  return pr == LB_FP64 ? tile_count_f64() : (pr == LB_FP32_SHIFTED ? tile_count_f32() : tile_count_f32h());
+  switch (h->p.precision) {
+    case LB_FP64: return tile_count_f64();
+    case LB_FP32_SHIFTED: return tile_count_f32();
+    case LB_FP32_FP16T: return tile_count_f32h();
+    default: return tile_count_df64();
+  }
 }
 
 TileChoice tile_info(const lb_handle* h, int k) {
-  const int pr = h->p.precision;
-  return pr == LB_FP64 ? tile_info_f64(k) : (pr == LB_FP32_SHIFTED ? tile_info_f32(k) : tile_info_f32h(k));
+  switch (h->p.precision) {
+    case LB_FP64: return tile_info_f64(k);
+    case LB_FP32_SHIFTED: return tile_info_f32(k);
+    case LB_FP32_FP16T: return tile_info_f32h(k);
+    default: return tile_info_df64(k);
+  }
 }
 
 cudaError_t init_buffer(const lb_handle* h, const double* fields, void* buf) {
-  const int pr = h->p.precision;
-  return pr == LB_FP64 ? init_f64(h->cfg, fields, buf, h->stream)
-                       : (pr == LB_FP32_SHIFTED ? init_f32(h->cfg, fields, buf, h->stream)
-                                                : init_f32h(h->cfg, fields, buf, h->stream));
+  switch (h->p.precision) {
+    case LB_FP64: return init_f64(h->cfg, fields, buf, h->stream);
+    case LB_FP32_SHIFTED: return init_f32(h->cfg, fields, buf, h->stream);
+    case LB_FP32_FP16T: return init_f32h(h->cfg, fields, buf, h->stream);
+    default: return init_df64(h->cfg, fields, buf, h->stream);
+  }
 }
 
 cudaError_t plane_get(const lb_handle* h, int k, const void* buf, double* out) {
-  const int pr = h->p.precision;
-  return pr == LB_FP64 ? plane_get_f64(h->cfg, k, buf, out, h->stream)
-                       : (pr == LB_FP32_SHIFTED ? plane_get_f32(h->cfg, k, buf, out, h->stream)
-                                                : plane_get_f32h(h->cfg, k, buf, out, h->stream));
+  switch (h->p.precision) {
+    case LB_FP64: return plane_get_f64(h->cfg, k, buf, out, h->stream);
+    case LB_FP32_SHIFTED: return plane_get_f32(h->cfg, k, buf, out, h->stream);
+    case LB_FP32_FP16T: return plane_get_f32h(h->cfg, k, buf, out, h->stream);
+    default: return plane_get_df64(h->cfg, k, buf, out, h->stream);
+  }
 }
 
 cudaError_t plane_put(const lb_handle* h, int k, const double* in, void* buf) {
-  const int pr = h->p.precision;
-  return pr == LB_FP64 ? plane_put_f64(h->cfg, k, in, buf, h->stream)
-                       : (pr == LB_FP32_SHIFTED ? plane_put_f32(h->cfg, k, in, buf, h->stream)
-                                                : plane_put_f32h(h->cfg, k, in, buf, h->stream));
+  switch (h->p.precision) {
+    case LB_FP64: return plane_put_f64(h->cfg, k, in, buf, h->stream);
+    case LB_FP32_SHIFTED: return plane_put_f32(h->cfg, k, in, buf, h->stream);
+    case LB_FP32_FP16T: return plane_put_f32h(h->cfg, k, in, buf, h->stream);
+    default: return plane_put_df64(h->cfg, k, in, buf, h->stream);
+  }
 }
 
 void drop_graphs(lb_handle* h) {
@@ -189,6 +205,7 @@ int lb_init(lb_handle** out, const lb_params* pin, const uint8_t* mask, const do
     return fail(nullptr, code, "%s", msg);
   };
   cudaError_t e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess && p.precision == LB_DF64) e = df_exp_tables_init();
   if (e != cudaSuccess) return bail(fail(h, LB_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
   e = cudaMemsetAsync(h->ws, 0, L.total, h->stream);  // buffers, partials and the error word start at zero
   if (e == cudaSuccess && mask) e = cudaMemcpyAsync(d_mask, mask, N, cudaMemcpyHostToDevice, h->stream);

@@ -426,7 +426,7 @@ int lb_batch_workspace_size(const lb_params* reps, int n, const int* has_mask, s
   for (int r = 0; r < n; ++r) {
     if (const char* why = check_params(&reps[r])) return bfail(nullptr, LB_EINVAL, "replica %d: %s", r, why);
     if (reps[r].precision != reps[0].precision) return bfail(nullptr, LB_EINVAL, "all replicas need one precision");
-    if (reps[r].precision == LB_FP32_FP16T)
+    if (reps[r].precision == LB_FP32_FP16T || reps[r].precision == LB_DF64)
       return bfail(nullptr, LB_EINVAL, "batched ensembles store LB_FP64 or LB_FP32_SHIFTED");
   }
   size_t a, c, d, e, f;
@@ -445,7 +445,7 @@ int lb_batch_init(lb_batch** out, const lb_params* reps, int n, const uint8_t* c
   for (int r = 0; r < n; ++r) {
     if (const char* why = check_params(&reps[r])) return bfail(nullptr, LB_EINVAL, "replica %d: %s", r, why);
     if (reps[r].precision != reps[0].precision) return bfail(nullptr, LB_EINVAL, "all replicas need one precision");
-    if (reps[r].precision == LB_FP32_FP16T)
+    if (reps[r].precision == LB_FP32_FP16T || reps[r].precision == LB_DF64)
       return bfail(nullptr, LB_EINVAL, "batched ensembles store LB_FP64 or LB_FP32_SHIFTED");
     has_mask[r] = masks && masks[r] ? 1 : 0;
     if (has_mask[r] && reps[r].periodic_y) return bfail(nullptr, LB_EINVAL, "replica %d: mask needs walls", r);

@@ -56,17 +56,21 @@ inline dim3 grid_for(int nx, int ny, int tx, int ty) {
 cudaError_t launch_f64(int mode, const StepCfg& c, const void* fin, void* fout, double* aux, cudaStream_t s);
 cudaError_t launch_f32(int mode, const StepCfg& c, const void* fin, void* fout, double* aux, cudaStream_t s);
 cudaError_t launch_f32h(int mode, const StepCfg& c, const void* fin, void* fout, double* aux, cudaStream_t s);
+cudaError_t launch_df64(int mode, const StepCfg& c, const void* fin, void* fout, double* aux, cudaStream_t s);
 // Initial rest equilibria from 3 planes (rho1, rho2, T) of nx*ny doubles.
 cudaError_t init_f64(const StepCfg& c, const double* fields, void* buf, cudaStream_t s);
 cudaError_t init_f32(const StepCfg& c, const double* fields, void* buf, cudaStream_t s);
 cudaError_t init_f32h(const StepCfg& c, const double* fields, void* buf, cudaStream_t s);
+cudaError_t init_df64(const StepCfg& c, const double* fields, void* buf, cudaStream_t s);
 // One population plane k to / from nx*ny doubles (full populations; solid nodes 0 / ignored).
 cudaError_t plane_get_f64(const StepCfg& c, int k, const void* buf, double* out, cudaStream_t s);
 cudaError_t plane_get_f32(const StepCfg& c, int k, const void* buf, double* out, cudaStream_t s);
 cudaError_t plane_get_f32h(const StepCfg& c, int k, const void* buf, double* out, cudaStream_t s);
+cudaError_t plane_get_df64(const StepCfg& c, int k, const void* buf, double* out, cudaStream_t s);
 cudaError_t plane_put_f64(const StepCfg& c, int k, const double* in, void* buf, cudaStream_t s);
 cudaError_t plane_put_f32(const StepCfg& c, int k, const double* in, void* buf, cudaStream_t s);
 cudaError_t plane_put_f32h(const StepCfg& c, int k, const double* in, void* buf, cudaStream_t s);
+cudaError_t plane_put_df64(const StepCfg& c, int k, const double* in, void* buf, cudaStream_t s);
 // Step-kernel tile candidates for the autotuner: tile TX x TY nodes, TX * BY threads, at least MINB
 // resident CTAs per SM requested from the compiler.  Candidate 0 is the default.
 struct TileChoice {
@@ -75,12 +79,28 @@ struct TileChoice {
 int tile_count_f64();
 int tile_count_f32();
 int tile_count_f32h();
+int tile_count_df64();
 TileChoice tile_info_f64(int k);
 TileChoice tile_info_f32(int k);
 TileChoice tile_info_f32h(int k);
+TileChoice tile_info_df64(int k);
 cudaError_t launch_step_tile_f64(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
 cudaError_t launch_step_tile_f32(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
 cudaError_t launch_step_tile_f32h(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
+cudaError_t launch_step_tile_df64(int k, const StepCfg& c, const void* fin, void* fout, cudaStream_t s);
+// The observables / fields launch of a precision form (LB_FP64 0, LB_FP32_SHIFTED 1, LB_FP32_FP16T 2,
+// LB_DF64 3).
+inline cudaError_t launch_mode(int precision, int mode, const StepCfg& c, const void* fin, void* fout, double* aux,
+                               cudaStream_t s) {
+  switch (precision) {
+    case 0: return launch_f64(mode, c, fin, fout, aux, s);
+    case 1: return launch_f32(mode, c, fin, fout, aux, s);
+    case 2: return launch_f32h(mode, c, fin, fout, aux, s);
+    default: return launch_df64(mode, c, fin, fout, aux, s);
+  }
+}
+// Double-float exp tables of the LB_DF64 form on the current device (once per device, before capture).
+cudaError_t df_exp_tables_init();
 // Error codes a kernel writes to StepCfg::err (the host maps them to LB_ETIMEOUT).
 constexpr int kErrWaitTimeout = 1;
 // Total shear stress (lb_stress.cu): the field mode writes rho_1, rho_2, T, u^(H) (5 planes of nx*ny

@@ -1,0 +1,201 @@
+// Double-float ("df") arithmetic for the LB_DF64 storage form: every value is an unevaluated sum
+// hi + lo of two FP32 numbers with |lo| <= ulp(hi) / 2, a 48-bit significand, and every operation runs
+// on the FP32 pipe.  On GB300 the FP64 pipe issues 2 operations per clock and SM, the FP32 pipe 128,
+// so a fused step in double-float arithmetic outruns the FP64 one although each operation takes
+// several FP32 instructions.
+//
+// The error-free transformations are the classical ones: the sum of two floats as s + e (Knuth's
+// two-sum, six operations; Dekker's fast two-sum, three, when |a| >= |b|) and their product as p + e
+// with one fused multiply-add (p = a b rounded, e = fma(a, b, -p)).  Every operation is written with
+// explicit round-to-nearest intrinsics, so the compiler contracts nothing and every kernel that calls
+// these functions computes the same bits.
+//
+// Storage: a population is a float2 (hi, lo) in memory, 8 bytes, the footprint of an FP64 value; no
+// conversion to or from FP64 happens in the step (on GB300 those conversions run at the FP64 rate).
+#pragma once
+#include <math.h>
+#include <stdint.h>
+
+#include "lb_kernels.cuh"
+
+namespace tlb {
+
+struct __align__(8) df {
+  float hi, lo;
+  df() = default;
+  __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr df(int v) : hi((float)v), lo(0.0f) {}
+  __host__ __device__ constexpr df(float v) : hi(v), lo(0.0f) {}
+  // round a double to the nearest double-float (exact for the 48 leading significand bits)
+  __host__ __device__ constexpr df(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+  __host__ __device__ explicit df(float2 v) : hi(v.x), lo(v.y) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+// Knuth two-sum: s + e = a + b exactly.
+__device__ __forceinline__ float df_two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+// Dekker fast two-sum, |a| >= |b| (or a = 0): s + e = a + b exactly.
+__device__ __forceinline__ float df_fast_two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+  return s;
+}
+// p + e = a b exactly.
+__device__ __forceinline__ float df_two_prod(float a, float b, float& e) {
+  const float p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+  return p;
+}
+
+// a + b, accurate also under cancellation: both parts are summed error-free.
+__device__ __forceinline__ df df_add(df a, df b) {
+  float e1, e2;
+  float s = df_two_sum(a.hi, b.hi, e1);
+  const float t = df_two_sum(a.lo, b.lo, e2);
+  e1 = __fadd_rn(e1, t);
+  s = df_fast_two_sum(s, e1, e1);
+  e1 = __fadd_rn(e1, e2);
+  s = df_fast_two_sum(s, e1, e1);
+  return df(s, e1);
+}
+__device__ __forceinline__ df df_neg(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df df_mul(df a, df b) {
+  float e;
+  float p = df_two_prod(a.hi, b.hi, e);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  p = df_fast_two_sum(p, e, e);
+  return df(p, e);
+}
+// a b + c with one renormalisation: the leading product and sum are error-free, the cross terms
+// and the low parts are summed in FP32.
+__device__ __forceinline__ df df_fma(df a, df b, df c) {
+  float e, e2;
+  const float p = df_two_prod(a.hi, b.hi, e);
+  float s = df_two_sum(p, c.hi, e2);
+  float t = __fmaf_rn(a.hi, b.lo, e);
+  t = __fmaf_rn(a.lo, b.hi, t);
+  t = __fadd_rn(t, c.lo);
+  t = __fadd_rn(t, e2);
+  s = df_fast_two_sum(s, t, t);
+  return df(s, t);
+}
+
+__device__ __forceinline__ df operator+(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ df operator-(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df operator-(df a) { return df_neg(a); }
+__device__ __forceinline__ df operator*(df a, df b) { return df_mul(a, b); }
+__device__ __forceinline__ df& operator+=(df& a, df b) { return a = df_add(a, b); }
+__device__ __forceinline__ bool operator>(df a, df b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ bool operator<(df a, df b) { return b > a; }
+
+// Lane pair of double-float values (two components, or a direction and its opposite), 16 bytes.
+struct __align__(16) df2 {
+  df x, y;
+};
+template <> struct V2T<df> { using type = df2; };
+
+__device__ __forceinline__ df2 p_add(df2 a, df2 b) { return df2{df_add(a.x, b.x), df_add(a.y, b.y)}; }
+__device__ __forceinline__ df2 p_sub(df2 a, df2 b) {
+  return df2{df_add(a.x, df_neg(b.x)), df_add(a.y, df_neg(b.y))};
+}
+__device__ __forceinline__ df2 p_mul(df2 a, df2 b) { return df2{df_mul(a.x, b.x), df_mul(a.y, b.y)}; }
+__device__ __forceinline__ df2 p_fma(df2 a, df2 b, df2 c) { return df2{df_fma(a.x, b.x, c.x), df_fma(a.y, b.y, c.y)}; }
+__device__ __forceinline__ df s_add(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ df s_mul(df a, df b) { return df_mul(a, b); }
+__device__ __forceinline__ df s_fma(df a, df b, df c) { return df_fma(a, b, c); }
+
+// Storage form: populations as (hi, lo) float pairs, arithmetic in double-float, no shift.
+struct DF {};
+template <> struct Storage<DF> {
+  using F = float2;
+  using G = float2;
+  using C = df;
+};
+template <> __device__ __forceinline__ df up<df, float2>(float2 v) { return df(v); }
+template <> __device__ __forceinline__ double up<double, float2>(float2 v) { return (double)v.x + (double)v.y; }
+template <> __device__ __forceinline__ float2 down<float2, df>(df v) { return make_float2(v.hi, v.lo); }
+template <> __device__ __forceinline__ float2 down<float2, double>(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+// D2Q9 weights as double-float constants: 4/9, 1/9, 1/36 split into their nearest float and the
+// float nearest to the remainder.
+template <> __host__ __device__ constexpr df wq<df>(int i) {
+  return i == 0 ? df(4.0 / 9.0) : (i <= 4 ? df(1.0 / 9.0) : df(1.0 / 36.0));
+}
+
+template <> struct Tile<df> { static constexpr int TX = 32, TY = 16, BY = 8; };
+template <> struct MinBlocks<df> { static constexpr int value = 2; };
+
+// 1 / x: an FP32 reciprocal refined by two Newton steps y <- y + y (1 - x y), the residual taken in
+// double-float; relative error about 2^-47.
+template <> __device__ __forceinline__ df recip<df>(df x) {
+  const float y0 = __fdividef(1.0f, x.hi);
+  float pe;
+  const float p = df_two_prod(x.hi, y0, pe);
+  pe = __fmaf_rn(x.lo, y0, pe);
+  const float e1 = __fsub_rn(__fsub_rn(1.0f, p), pe);  // 1 - p is exact: p is within a few ulps of 1
+  float l1;
+  const float h1 = df_fast_two_sum(y0, __fmul_rn(y0, e1), l1);
+  const df y1(h1, l1);
+  const df q = df_mul(x, y1);
+  const float e2 = __fsub_rn(__fsub_rn(1.0f, q.hi), q.lo);
+  return df_add(y1, df(__fmul_rn(y1.hi, e2), 0.0f));
+}
+
+// ---- exp(-x) for the pseudo-potential psi = rho0 (1 - exp(-rho / rho0)) ----
+// Two-level table: x = n / 4096 + r with n = rint(4096 x), |r| <= 2^-13;
+// exp(-x) = T1[n >> 6] T2[n & 63] exp(-r), T1[k] = exp(-k / 64) (k = 0..256), T2[j] = exp(-j / 4096)
+// (j = 0..63), and exp(-r) = 1 - r + r^2 / 2 - r^3 / 6 + r^4 / 24 (the next term is below 2^-70).
+// The tables are double-float roundings of FP64 exp values, written by the host before the first
+// step (df_exp_tables_init).  Arguments outside [0, 4) take an FP64 exp instead.  The tables are
+// defined here: one translation unit (lb_df64.cu) includes this header.
+constexpr int kDfExpT1 = 257, kDfExpT2 = 64;
+__device__ float2 g_df_exp_t1[kDfExpT1];
+__device__ float2 g_df_exp_t2[kDfExpT2];
+cudaError_t df_exp_tables_init();
+
+__device__ __forceinline__ df df_exp_neg(df x) {
+  const float t = __fmul_rn(x.hi, 4096.0f);
+  if (!(x.hi >= 0.0f) || !(t < 16384.0f)) {
+    const double v = exp(-(double)x);
+    const float h = __double2float_rn(v);
+    return df(h, __double2float_rn(v - (double)h));
+  }
+  // rint(t) by the 1.5 * 2^23 shift: exact for 0 <= t < 2^22
+  const float m = __fadd_rn(t, 12582912.0f);
+  const int n = __float_as_int(m) - 0x4B400000;
+  const float nf = __fmul_rn(__fsub_rn(m, 12582912.0f), 1.0f / 4096.0f);  // n / 4096, exact
+  float rl;
+  const float rh = df_two_sum(__fsub_rn(x.hi, nf), x.lo, rl);  // x.hi - n / 4096 is exact (Sterbenz)
+  // r^2 / 2 in double-float, r^3 / 6 and r^4 / 24 in FP32
+  float r2l;
+  const float r2h = df_two_prod(rh, rh, r2l);
+  r2l = __fmaf_rn(2.0f * rh, rl, r2l);
+  const float small = __fmaf_rn(__fmul_rn(r2h, r2h), 1.0f / 24.0f, -__fmul_rn(__fmul_rn(r2h, rh), 1.0f / 6.0f));
+  // 1 - r + r^2 / 2 + small; |r| <= 2^-13, so the leading 1 dominates every other term
+  float e;
+  const float s = df_two_sum(1.0f, -rh, e);
+  e = __fadd_rn(e, -rl);
+  e = __fadd_rn(e, __fmul_rn(0.5f, r2h));
+  e = __fadd_rn(e, __fadd_rn(__fmul_rn(0.5f, r2l), small));
+  float el;
+  const float eh = df_fast_two_sum(s, e, el);
+  const df er(eh, el);
+  const df t1(__ldg(&g_df_exp_t1[n >> 6])), t2(__ldg(&g_df_exp_t2[n & 63]));
+  return df_mul(df_mul(t1, t2), er);
+}
+
+template <> __device__ __forceinline__ df psi_exp<df>(df rho, df rho0, df inv_rho0) {
+  const df e = df_exp_neg(df_mul(rho, inv_rho0));
+  return df_add(rho0, df_neg(df_mul(rho0, e)));
+}
+
+}  // namespace tlb

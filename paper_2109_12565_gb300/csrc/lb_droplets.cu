@@ -810,6 +810,7 @@ int dfail(lb_handle* h, int code, const char* msg, cudaError_t e = cudaSuccess) 
 
 cudaError_t fields_into(const lb_handle* h, double* stage) {
   const int pr = h->p.precision;
+  if (pr == LB_DF64) return launch_df64(MODE_FIELDS, h->cfg, h->buf[h->cur], nullptr, stage, h->stream);
   return pr == LB_FP64 ? launch_f64(MODE_FIELDS, h->cfg, h->buf[h->cur], nullptr, stage, h->stream)
                        : (pr == LB_FP32_SHIFTED ? launch_f32(MODE_FIELDS, h->cfg, h->buf[h->cur], nullptr, stage, h->stream)
                                                 : launch_f32h(MODE_FIELDS, h->cfg, h->buf[h->cur], nullptr, stage, h->stream));

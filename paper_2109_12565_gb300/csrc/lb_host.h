@@ -23,16 +23,21 @@ struct Layout {
   int n_blocks = 0;
 };
 
-inline int obs_tile_x(int precision) { return precision == LB_FP64 ? Tile<double>::TX : Tile<float>::TX; }
-inline int obs_tile_y(int precision) { return precision == LB_FP64 ? Tile<double>::TY : Tile<float>::TY; }
+// 8-byte population storage (FP64, or double-float pairs) versus the FP32 forms.
+inline bool wide_storage(int precision) { return precision == LB_FP64 || precision == LB_DF64; }
+// Forms that store deviations from the shift equilibria.
+inline bool shifted_storage(int precision) { return precision == LB_FP32_SHIFTED || precision == LB_FP32_FP16T; }
+inline int obs_tile_x(int precision) { return wide_storage(precision) ? Tile<double>::TX : Tile<float>::TX; }
+inline int obs_tile_y(int precision) { return wide_storage(precision) ? Tile<double>::TY : Tile<float>::TY; }
 
 inline const char* check_params(const lb_params* p) {
   if (!p) return "params is NULL";
   if (p->nx < 1 || p->ny < 1) return "nx and ny must be >= 1";
   if ((long long)p->nx * p->ny > (1LL << 31) - 1) return "nx * ny must fit in 31 bits";
   if (!p->periodic_y && p->ny < 3) return "walls (periodic_y = 0) need ny >= 3";
-  if (p->precision != LB_FP64 && p->precision != LB_FP32_SHIFTED && p->precision != LB_FP32_FP16T)
-    return "precision must be LB_FP64, LB_FP32_SHIFTED or LB_FP32_FP16T";
+  if (p->precision != LB_FP64 && p->precision != LB_FP32_SHIFTED && p->precision != LB_FP32_FP16T &&
+      p->precision != LB_DF64)
+    return "precision must be LB_FP64, LB_FP32_SHIFTED, LB_FP32_FP16T or LB_DF64";
   if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return "tau must be finite and > 1/2";
   if (!(p->tau_g > 0.5) || !std::isfinite(p->tau_g)) return "tau_g must be finite and > 1/2";
   if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0)) return "rho0 must be finite and > 0";
@@ -43,7 +48,7 @@ inline const char* check_params(const lb_params* p) {
   if (!(p->rho_wall[0] > 0.0) || !(p->rho_wall[1] > 0.0) || !std::isfinite(p->rho_wall[0]) ||
       !std::isfinite(p->rho_wall[1]))
     return "rho_wall must be finite and > 0";
-  const int per_row = p->precision == LB_FP64 ? 16 : 32;
+  const int per_row = wide_storage(p->precision) ? 16 : 32;
   const double pitch = (double)((p->nx + per_row - 1) / per_row * per_row);
   if (27.0 * pitch * (double)p->ny >= 2147483648.0) return "lattice too large: 27 * pitch * ny must stay below 2^31";
   return nullptr;
@@ -51,7 +56,7 @@ inline const char* check_params(const lb_params* p) {
 
 inline Layout layout_for(const lb_params* p, int has_mask) {
   Layout L;
-  L.elem = p->precision == LB_FP64 ? 8 : 4;
+  L.elem = wide_storage(p->precision) ? 8 : 4;
   const int per_row = (int)(128 / L.elem);
   L.pitch = (p->nx + per_row - 1) / per_row * per_row;
   const size_t plane = (size_t)L.pitch * p->ny;
@@ -108,7 +113,7 @@ inline StepCfg make_stepcfg(const lb_params& p, int pitch, const uint8_t* d_mask
   c.alpha_g = p.alpha_g;
   c.body_fx = p.body_fx;
   c.rho_bar[0] = c.rho_bar[1] = c.T_bar = 0.0;
-  if (p.precision != LB_FP64) {
+  if (shifted_storage(p.precision)) {
     c.rho_bar[0] = p.shift_rho[0];
     c.rho_bar[1] = p.shift_rho[1];
     c.T_bar = p.shift_T;
@@ -145,7 +150,7 @@ inline const char* prepare_fields(lb_params& p, const uint8_t* mask, const doubl
       ++nf;
     }
   if (nf == 0) return "the lattice has no fluid node";
-  if (p.precision != LB_FP64) {
+  if (shifted_storage(p.precision)) {
     if (std::isnan(p.shift_rho[0])) p.shift_rho[0] = sum1 / (double)nf;
     if (std::isnan(p.shift_rho[1])) p.shift_rho[1] = sum2 / (double)nf;
     if (std::isnan(p.shift_T)) p.shift_T = 0.5 * (p.T_down + p.T_up);

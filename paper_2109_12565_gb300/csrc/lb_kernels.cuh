@@ -461,7 +461,7 @@ template <class C> struct StencilSums {
 template <class C>
 __device__ __forceinline__ void sums_row0(StencilSums<C>& a, const KParams<C>& kp, const V2<C> p[5], V2<C> rm,
                                           V2<C> rp) {
-  a.qx = p_mul(splat<C>(C(1) / C(9)), p_sub(rp, rm));
+  a.qx = p_mul(splat<C>(wq<C>(1)), p_sub(rp, rm));
   a.sx = p_fma(v2<C>(kp.a4x2[0], kp.a4x2[1]), p_sub(p[4], p[0]),
                p_mul(v2<C>(kp.a1[0], kp.a1[1]), p_sub(p[3], p[1])));
 }
@@ -472,7 +472,7 @@ template <class C>
 __device__ __forceinline__ void sums_row1(StencilSums<C>& a, const KParams<C>& kp, const V2<C> pu[5],
                                           const V2<C> pd[5], const V2<C> ru[3], const V2<C> rd[3]) {
   using V = V2<C>;
-  const V w1 = splat<C>(C(1) / C(9)), w2 = splat<C>(C(1) / C(36));
+  const V w1 = splat<C>(wq<C>(1)), w2 = splat<C>(wq<C>(5));
   const V e01 = p_sub(ru[1], rd[1]), e11 = p_sub(ru[2], rd[0]), em1 = p_sub(ru[0], rd[2]);
   a.qx = p_fma(w2, p_sub(e11, em1), a.qx);
   a.qy = p_fma(w2, p_add(e11, em1), p_mul(w1, e01));

@@ -202,9 +202,7 @@ cudaError_t stress_run(const StepCfg& cfg_in, int precision, const void* cur, do
                        double** d_rows, double** d_tot) {
   const int nx = cfg_in.nx, ny = cfg_in.ny;
   const size_t N = (size_t)nx * ny;
-  cudaError_t e = precision == LB_FP64 ? launch_f64(MODE_FIELDS, cfg_in, cur, nullptr, stage, s)
-                  : precision == LB_FP32_SHIFTED ? launch_f32(MODE_FIELDS, cfg_in, cur, nullptr, stage, s)
-                                                 : launch_f32h(MODE_FIELDS, cfg_in, cur, nullptr, stage, s);
+  cudaError_t e = launch_mode(precision, MODE_FIELDS, cfg_in, cur, nullptr, stage, s);
   if (e != cudaSuccess) return e;
   // the fields are full values: constants without storage shifts
   StepCfg c = cfg_in;

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtlbgb300.so")
 
 LB_OK, LB_EINVAL, LB_ENOSPACE, LB_ECUDA, LB_ETIMEOUT, LB_EUNSTABLE = 0, -1, -2, -3, -4, -5
-LB_FP64, LB_FP32_SHIFTED, LB_FP32_FP16T = 0, 1, 2
+LB_FP64, LB_FP32_SHIFTED, LB_FP32_FP16T, LB_DF64 = 0, 1, 2, 3
 _NAMES = {0: "LB_OK", -1: "LB_EINVAL", -2: "LB_ENOSPACE", -3: "LB_ECUDA", -4: "LB_ETIMEOUT", -5: "LB_EUNSTABLE"}
 
 # every symbol include/tlb.h declares

@@ -52,6 +52,8 @@ def test_workspace_size_layout():
     big = I.emulsion_1024x512()
     assert lb.workspace_size(big.params, False, lb.LB_FP64) < 2 * 27 * 1024 * 512 * 8 * 1.01
     # FP32 fluid + FP16 thermal: 18 * 4 + 9 * 2 = 90 bytes per node and buffer
+    # double-float pairs take the FP64 footprint
+    assert lb.workspace_size(big.params, False, lb.LB_DF64) == lb.workspace_size(big.params, False, lb.LB_FP64)
     n16 = lb.workspace_size(big.params, False, lb.LB_FP32_FP16T)
     assert 2 * 90 * 1024 * 512 <= n16 < 2 * 90 * 1024 * 512 * 1.01
     assert n16 < lb.workspace_size(big.params, False, lb.LB_FP32_SHIFTED)

@@ -40,13 +40,17 @@ def _max_field_diff(fg, fo, keys=("rho1", "rho2", "T", "ux", "uy")):
     return {k: float(np.abs(fg[k] - fo[k]).max()) for k in keys}
 
 
-def test_fp64_emulsion_64x64_1000_steps_matches_oracle():
+@pytest.mark.parametrize("precision", [lb.LB_FP64, lb.LB_DF64])
+def test_fp64_emulsion_64x64_1000_steps_matches_oracle(precision):
+    """FP64 storage, and double-float storage and arithmetic (LB_DF64), against the FP64 oracle: both
+    held to the FP64 bound of 1e-11 after 1000 steps."""
     w = I.emulsion_small()
-    g, o = _pair(w.params, w.rho1, w.rho2, w.T0)
+    g, o = _pair(w.params, w.rho1, w.rho2, w.T0, precision=precision)
     g.step(1000)
     o.step(1000)
     d_state = np.abs(g.get_state() - o.state).max()
     d = _max_field_diff(g.fields(), o.fields())
+    print(f"precision {precision}: max |GPU - oracle| state {d_state:.3e}")
     assert d_state <= 1e-11, d_state
     assert max(d.values()) <= 1e-11, d
     og, oo = g.observables(), o.observables()
@@ -59,6 +63,7 @@ def test_fp64_emulsion_64x64_1000_steps_matches_oracle():
     assert oo["E"] > 1e-10 and abs(oo["Nu"] - 1.0) > 1e-4
 
 
+@pytest.mark.parametrize("precision", [lb.LB_FP64, lb.LB_DF64])
 @pytest.mark.parametrize("nx,ny,periodic,posts", [
     (37, 21, 0, True),    # ragged in x and y against the 32x16 / 64x16 tiles, posts on both walls
     (70, 35, 1, False),   # periodic, several tiles with ragged tails
@@ -67,7 +72,10 @@ def test_fp64_emulsion_64x64_1000_steps_matches_oracle():
     (5, 7, 0, False),     # narrower than the 5-wide stencil: x wraps onto itself
     (129, 40, 0, True),
 ])
-def test_fp64_small_and_ragged_lattices(nx, ny, periodic, posts):
+def test_fp64_small_and_ragged_lattices(precision, nx, ny, periodic, posts):
+    """FP64 within 1e-12 of the oracle after 200 steps; LB_DF64 (48-bit significand) within the FP64
+    form's bound, 1e-11."""
+    tol = 1e-12 if precision == lb.LB_FP64 else 1e-11
     R = min(nx, ny) / 5.0
     w = I.emulsion_small(nx=nx, ny=ny, n_drops=1, R=max(R, 1.5)) if not periodic else None
     if periodic:
@@ -82,14 +90,14 @@ def test_fp64_small_and_ragged_lattices(nx, ny, periodic, posts):
         params, r1, r2, T0 = w.params, w.rho1, w.rho2, w.T0
         params = dict(params, alpha_g=1e-3)
         mask = I.posts_mask(nx, ny, 2, 3, 7) if posts else None
-    g, o = _pair(params, r1, r2, T0, mask=mask)
+    g, o = _pair(params, r1, r2, T0, mask=mask, precision=precision)
     for n in (1, 16, 183):
         g.step(n)
         o.step(n)
         d_state = np.abs(g.get_state() - o.state).max()
-        assert d_state <= 1e-12, (n, d_state)
+        assert d_state <= tol, (n, d_state)
     d = _max_field_diff(g.fields(), o.fields())
-    assert max(d.values()) <= 1e-12, d
+    assert max(d.values()) <= tol, d
     og, oo = g.observables(), o.observables()
     np.testing.assert_allclose(og["mass"], oo["mass"], rtol=1e-13)
     assert abs(og["Nu"] - oo["Nu"]) <= 1e-10
@@ -331,7 +339,7 @@ def test_init_errors():
     assert e.value.code == lb.LB_EINVAL
 
 
-@pytest.mark.parametrize("precision", [lb.LB_FP64, lb.LB_FP32_SHIFTED, lb.LB_FP32_FP16T])
+@pytest.mark.parametrize("precision", [lb.LB_FP64, lb.LB_FP32_SHIFTED, lb.LB_FP32_FP16T, lb.LB_DF64])
 @pytest.mark.parametrize("periodic", [0, 1])
 @pytest.mark.parametrize("nx,ny", [(300, 130), (277, 45)])
 def test_every_tile_candidate_gives_identical_results(precision, periodic, nx, ny):

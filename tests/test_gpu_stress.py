@@ -51,7 +51,8 @@ def _compare(g, p, state, mask, tol):
 
 
 @pytest.mark.parametrize("case", [0, 1, 2])
-@pytest.mark.parametrize("precision,tol", [(lb.LB_FP64, 1e-10), (lb.LB_FP32_SHIFTED, 1e-3), (lb.LB_FP32_FP16T, 1e-3)])
+@pytest.mark.parametrize("precision,tol", [(lb.LB_FP64, 1e-10), (lb.LB_DF64, 1e-10), (lb.LB_FP32_SHIFTED, 1e-3),
+                                           (lb.LB_FP32_FP16T, 1e-3)])
 def test_stress_matches_oracle(case, precision, tol):
     name, p, w, mask = list(_cases())[case]
     o = O.Oracle(p, w.rho1, w.rho2, w.T0, mask=mask)
