@@ -100,13 +100,83 @@ struct __align__(16) df2 {
 };
 template <> struct V2T<df> { using type = df2; };
 
-__device__ __forceinline__ df2 p_add(df2 a, df2 b) { return df2{df_add(a.x, b.x), df_add(a.y, b.y)}; }
-__device__ __forceinline__ df2 p_sub(df2 a, df2 b) {
-  return df2{df_add(a.x, df_neg(b.x)), df_add(a.y, df_neg(b.y))};
+// The lane-pair operations run the double-float algorithms above on packed FP32x2 instructions (one
+// instruction for both lanes, each lane rounding once), so each lane equals the scalar operation.
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 f2_two_sum(float2 a, float2 b, float2& e) {
+  const float2 s = f2_add(a, b);
+  const float2 bb = f2_sub(s, a);
+  e = f2_add(f2_sub(a, f2_sub(s, bb)), f2_sub(b, bb));
+  return s;
 }
-__device__ __forceinline__ df2 p_mul(df2 a, df2 b) { return df2{df_mul(a.x, b.x), df_mul(a.y, b.y)}; }
-__device__ __forceinline__ df2 p_fma(df2 a, df2 b, df2 c) { return df2{df_fma(a.x, b.x, c.x), df_fma(a.y, b.y, c.y)}; }
+__device__ __forceinline__ float2 f2_fast_two_sum(float2 a, float2 b, float2& e) {
+  const float2 s = f2_add(a, b);
+  e = f2_sub(b, f2_sub(s, a));
+  return s;
+}
+__device__ __forceinline__ float2 hi2(df2 a) { return make_float2(a.x.hi, a.y.hi); }
+__device__ __forceinline__ float2 lo2(df2 a) { return make_float2(a.x.lo, a.y.lo); }
+__device__ __forceinline__ df2 make_df2(float2 h, float2 l) { return df2{df(h.x, l.x), df(h.y, l.y)}; }
+
+__device__ __forceinline__ df2 p_add(df2 a, df2 b) {
+  float2 e1, e2;
+  float2 s = f2_two_sum(hi2(a), hi2(b), e1);
+  const float2 t = f2_two_sum(lo2(a), lo2(b), e2);
+  e1 = f2_add(e1, t);
+  s = f2_fast_two_sum(s, e1, e1);
+  e1 = f2_add(e1, e2);
+  s = f2_fast_two_sum(s, e1, e1);
+  return make_df2(s, e1);
+}
+__device__ __forceinline__ df2 p_acc(df2 a, df2 b) {  // df_add_same_sign per lane, packed
+  float2 e;
+  const float2 s = f2_two_sum(hi2(a), hi2(b), e);
+  e = f2_add(e, f2_add(lo2(a), lo2(b)));
+  float2 l;
+  const float2 h = f2_fast_two_sum(s, e, l);
+  return make_df2(h, l);
+}
+__device__ __forceinline__ df2 p_sub(df2 a, df2 b) {
+  const float2 bh = hi2(b), bl = lo2(b);
+  return p_add(a, make_df2(make_float2(-bh.x, -bh.y), make_float2(-bl.x, -bl.y)));
+}
+__device__ __forceinline__ df2 p_mul(df2 a, df2 b) {
+  const float2 ah = hi2(a), bh = hi2(b);
+  const float2 p = __fmul2_rn(ah, bh);
+  float2 e = __ffma2_rn(ah, bh, make_float2(-p.x, -p.y));
+  e = __ffma2_rn(ah, lo2(b), e);
+  e = __ffma2_rn(lo2(a), bh, e);
+  float2 l;
+  const float2 h = f2_fast_two_sum(p, e, l);
+  return make_df2(h, l);
+}
+__device__ __forceinline__ df2 p_fma(df2 a, df2 b, df2 c) {
+  const float2 ah = hi2(a), bh = hi2(b);
+  const float2 p = __fmul2_rn(ah, bh);
+  const float2 e = __ffma2_rn(ah, bh, make_float2(-p.x, -p.y));
+  float2 e2;
+  const float2 sh = f2_two_sum(p, hi2(c), e2);
+  float2 t = __ffma2_rn(ah, lo2(b), e);
+  t = __ffma2_rn(lo2(a), bh, t);
+  t = f2_add(t, lo2(c));
+  t = f2_add(t, e2);
+  float2 l;
+  const float2 h = f2_fast_two_sum(sh, t, l);
+  return make_df2(h, l);
+}
 __device__ __forceinline__ df s_add(df a, df b) { return df_add(a, b); }
+// a + b for operands of one sign: one two-sum of the leading parts, the low parts summed in FP32; the
+// error stays below 2^-47 |a + b| when no cancellation can occur.
+__device__ __forceinline__ df df_add_same_sign(df a, df b) {
+  float e;
+  const float s = df_two_sum(a.hi, b.hi, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  float l;
+  const float h = df_fast_two_sum(s, e, l);
+  return df(h, l);
+}
+__device__ __forceinline__ df s_acc(df a, df b) { return df_add_same_sign(a, b); }
 __device__ __forceinline__ df s_mul(df a, df b) { return df_mul(a, b); }
 __device__ __forceinline__ df s_fma(df a, df b, df c) { return df_fma(a, b, c); }
 
@@ -116,6 +186,7 @@ template <> struct Storage<DF> {
   using F = float2;
   using G = float2;
   using C = df;
+  static constexpr bool kFastPath = false;  // one phase B: the step is bound by arithmetic and code size
 };
 template <> __device__ __forceinline__ df up<df, float2>(float2 v) { return df(v); }
 template <> __device__ __forceinline__ double up<double, float2>(float2 v) { return (double)v.x + (double)v.y; }
@@ -196,6 +267,49 @@ __device__ __forceinline__ df df_exp_neg(df x) {
 template <> __device__ __forceinline__ df psi_exp<df>(df rho, df rho0, df inv_rho0) {
   const df e = df_exp_neg(df_mul(rho, inv_rho0));
   return df_add(rho0, df_neg(df_mul(rho0, e)));
+}
+
+}  // namespace tlb
+
+namespace tlb {
+
+// psi of both components with the arithmetic of psi_exp<df> on packed FP32x2 instructions (per lane the
+// same operations, so the same bits); the table lookups stay per lane, and a lane outside the table
+// range is recomputed by the scalar path (FP64 exp).
+template <> __device__ __forceinline__ df2 psi_exp_pair<df>(df2 rho, df rho0, df inv_rho0) {
+  const df2 x = p_mul(rho, df2{inv_rho0, inv_rho0});
+  const float2 xh = hi2(x), xl = lo2(x);
+  const float2 t = __fmul2_rn(xh, make_float2(4096.0f, 4096.0f));
+  const bool ok0 = xh.x >= 0.0f && t.x < 16384.0f, ok1 = xh.y >= 0.0f && t.y < 16384.0f;
+  const float2 tc = make_float2(ok0 ? t.x : 0.0f, ok1 ? t.y : 0.0f);
+  const float2 xhc = make_float2(ok0 ? xh.x : 0.0f, ok1 ? xh.y : 0.0f);
+  const float2 xlc = make_float2(ok0 ? xl.x : 0.0f, ok1 ? xl.y : 0.0f);
+  const float2 shift = make_float2(12582912.0f, 12582912.0f);
+  const float2 m = f2_add(tc, shift);
+  const int n0 = __float_as_int(m.x) - 0x4B400000, n1 = __float_as_int(m.y) - 0x4B400000;
+  const float2 nf = __fmul2_rn(f2_sub(m, shift), make_float2(1.0f / 4096.0f, 1.0f / 4096.0f));
+  float2 rl;
+  const float2 rh = f2_two_sum(f2_sub(xhc, nf), xlc, rl);
+  const float2 r2h = __fmul2_rn(rh, rh);
+  float2 r2l = __ffma2_rn(rh, rh, make_float2(-r2h.x, -r2h.y));
+  r2l = __ffma2_rn(__fmul2_rn(make_float2(2.0f, 2.0f), rh), rl, r2l);
+  const float2 c3 = __fmul2_rn(__fmul2_rn(r2h, rh), make_float2(1.0f / 6.0f, 1.0f / 6.0f));
+  const float2 small = __ffma2_rn(__fmul2_rn(r2h, r2h), make_float2(1.0f / 24.0f, 1.0f / 24.0f), make_float2(-c3.x, -c3.y));
+  float2 e;
+  const float2 s = f2_two_sum(make_float2(1.0f, 1.0f), make_float2(-rh.x, -rh.y), e);
+  e = f2_add(e, make_float2(-rl.x, -rl.y));
+  e = f2_add(e, __fmul2_rn(make_float2(0.5f, 0.5f), r2h));
+  e = f2_add(e, f2_add(__fmul2_rn(make_float2(0.5f, 0.5f), r2l), small));
+  float2 el;
+  const float2 eh = f2_fast_two_sum(s, e, el);
+  const df2 t1{df(__ldg(&g_df_exp_t1[n0 >> 6])), df(__ldg(&g_df_exp_t1[n1 >> 6]))};
+  const df2 t2{df(__ldg(&g_df_exp_t2[n0 & 63])), df(__ldg(&g_df_exp_t2[n1 & 63]))};
+  const df2 E = p_mul(p_mul(t1, t2), make_df2(eh, el));
+  const df2 r0{rho0, rho0};
+  df2 psi = p_sub(r0, p_mul(r0, E));
+  if (!ok0) psi.x = psi_exp<df>(rho.x, rho0, inv_rho0);
+  if (!ok1) psi.y = psi_exp<df>(rho.y, rho0, inv_rho0);
+  return psi;
 }
 
 }  // namespace tlb

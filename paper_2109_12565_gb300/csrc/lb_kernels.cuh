@@ -49,15 +49,19 @@ template <class C> __host__ __device__ constexpr C wq(int i) { return i == 0 ? C
 // equilibria), arithmetic in FP32.  A buffer is the 18 fluid planes followed by the 9 thermal planes,
 // each of `plane` elements of its own type.
 struct F32H16 {};
+// kFastPath: also instantiate the interior fast path of phase B (unconditional stores); a form whose
+// arithmetic dominates (double-float) keeps one phase B, halving its code.
 template <class S> struct Storage {
   using F = S;  // fluid planes
   using G = S;  // thermal planes
   using C = S;  // arithmetic
+  static constexpr bool kFastPath = true;
 };
 template <> struct Storage<F32H16> {
   using F = float;
   using G = __half;
   using C = float;
+  static constexpr bool kFastPath = true;
 };
 template <class S> using SF = typename Storage<S>::F;
 template <class S> using SG = typename Storage<S>::G;
@@ -199,6 +203,11 @@ template <class V> __device__ __forceinline__ V swap_lanes(const V& v) {
   return r;
 }
 
+// psi of both components (lanes), one psi_exp per lane.
+template <class C> __device__ __forceinline__ V2<C> psi_exp_pair(V2<C> rho, C rho0, C inv_rho0) {
+  return v2<C>(psi_exp<C>(rho.x, rho0, inv_rho0), psi_exp<C>(rho.y, rho0, inv_rho0));
+}
+
 // Lane-wise arithmetic on pairs: one packed FP32x2 instruction in FP32, one instruction per lane in
 // FP64.  Each operation rounds once to nearest, so every lane holds exactly the result of the scalar
 // operation (a - b is the fused b * (-1) + a, exact up to its one rounding).
@@ -217,6 +226,9 @@ __device__ __forceinline__ double2 p_fma(double2 a, double2 b, double2 c) {
 template <class V> __device__ __forceinline__ V p_sub(V a, V b) {
   return p_fma(b, splat<decltype(a.x)>(decltype(a.x)(-1)), a);
 }
+// Accumulation of terms of one sign (the nine populations of a density, the thermal populations of a
+// node): a form with compound arithmetic may use a shorter sum there; for FP32 and FP64 it is the add.
+template <class V> __device__ __forceinline__ V p_acc(V a, V b) { return p_add(a, b); }
 // Scalar operations with one rounding each, never fused beyond what is written, so that every caller
 // of the functions below computes the same bits.
 __device__ __forceinline__ float s_add(float a, float b) { return __fadd_rn(a, b); }
@@ -225,6 +237,7 @@ __device__ __forceinline__ float s_fma(float a, float b, float c) { return __fma
 __device__ __forceinline__ double s_add(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double s_mul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double s_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <class C> __device__ __forceinline__ C s_acc(C a, C b) { return s_add(a, b); }
 
 template <class C, int TX, int TY, bool NEED_T> struct alignas(16) TileSmem {
   static constexpr int RX = TX + 4, RY = TY + 4;
@@ -414,23 +427,20 @@ __device__ __forceinline__ bool tile_phase_a(const SF<S>* __restrict__ fin, cons
       sm.solid[ry][rx] = 1;
     } else {
       const SF<S>* src = fin + (gy * pitch + gx);
-      C f[9], h[9];
+      // lanes = the two components: each lane runs the sums of one component in the order written
+      V2<C> u[9];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        f[i] = C(ld_pop<CG>(src + i * plane));
-        h[i] = C(ld_pop<CG>(src + (9 + i) * plane));
-      }
-      C d1 = C(0), d2 = C(0);
+      for (int i = 0; i < 9; ++i) u[i] = v2<C>(C(ld_pop<CG>(src + i * plane)), C(ld_pop<CG>(src + (9 + i) * plane)));
+      V2<C> d = splat<C>(C(0));
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        d1 += f[i];
-        d2 += h[i];
-      }
-      sm.rho[ry][rx] = v2<C>(d1, d2);
-      sm.psi[ry][rx] = v2<C>(psi_exp<C>(d1 + rb0, kp.rho0, kp.inv_rho0), psi_exp<C>(d2 + rb1, kp.rho0, kp.inv_rho0));
+      for (int i = 0; i < 9; ++i) d = p_acc(d, u[i]);
+      sm.rho[ry][rx] = d;
+      sm.psi[ry][rx] = psi_exp_pair<C>(p_add(d, v2<C>(rb0, rb1)), kp.rho0, kp.inv_rho0);
       if (rx >= 2 && rx < TX + 2 && ry >= 2 && ry < TY + 2) {
-        sm.jx[ry - 2][rx - 2] = (f[1] - f[3] + f[5] - f[6] - f[7] + f[8]) + (h[1] - h[3] + h[5] - h[6] - h[7] + h[8]);
-        sm.jy[ry - 2][rx - 2] = (f[2] - f[4] + f[5] + f[6] - f[7] - f[8]) + (h[2] - h[4] + h[5] + h[6] - h[7] - h[8]);
+        const V2<C> jx = p_add(p_sub(p_sub(p_add(p_sub(u[1], u[3]), u[5]), u[6]), u[7]), u[8]);
+        const V2<C> jy = p_sub(p_sub(p_add(p_add(p_sub(u[2], u[4]), u[5]), u[6]), u[7]), u[8]);
+        sm.jx[ry - 2][rx - 2] = s_add(jx.x, jx.y);
+        sm.jy[ry - 2][rx - 2] = s_add(jy.x, jy.y);
       }
       if constexpr (NEED_T) {
         C t = C(0);
@@ -753,7 +763,7 @@ __device__ __forceinline__ NodeMoments<C> node_moments(const SMT& sm, const KPar
   m.r2 = SHIFT ? m.dr2 + kp.rho_bar[1] : m.dr2;
   m.dT = C(0);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) m.dT += g[i];
+  for (int i = 0; i < 9; ++i) m.dT = s_acc(m.dT, g[i]);
   m.T = m.dT + (SHIFT ? kp.T_bar : C(0));
   m.jx = sm.jx[ty][tx];
   m.jy = sm.jy[ty][tx];
@@ -884,10 +894,13 @@ __device__ __forceinline__ void tile_step(const SF<S>* __restrict__ fin, SF<S>* 
   const int tid = threadIdx.y * TX + threadIdx.x;
   const bool fast = tile_phase_a<S, C, SHIFT, mode_needs_T(MODE), TX, TY, NT, CG>(fin, kp, x0, y0, sm, tid);
   const GlobalPopSource<S, CG> pop{fin, kp.plane};
-  if (mode_steps(MODE) && fast)
-    tile_phase_b<S, C, SHIFT, MODE, true, TX, TY, BY>(pop, fout, kp, x0, y0, sm, aux, acc);
-  else
-    tile_phase_b<S, C, SHIFT, MODE, false, TX, TY, BY>(pop, fout, kp, x0, y0, sm, aux, acc);
+  if constexpr (Storage<S>::kFastPath) {
+    if (mode_steps(MODE) && fast) {
+      tile_phase_b<S, C, SHIFT, MODE, true, TX, TY, BY>(pop, fout, kp, x0, y0, sm, aux, acc);
+      return;
+    }
+  }
+  tile_phase_b<S, C, SHIFT, MODE, false, TX, TY, BY>(pop, fout, kp, x0, y0, sm, aux, acc);
 }
 
 // Block-wide deterministic sum of the observable accumulators into aux[slot * kObsSlots + v].
