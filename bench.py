@@ -82,7 +82,7 @@ def rnd(v, digits=5):
 
 
 # sources that define the step kernels (their DRAM counters go stale when one of these changes)
-STEP_KERNEL_SOURCES = ("lb_cfg.h", "lb_kernels.cuh", "lb_f32.cu", "lb_f64.cu", "lb_f32h.cu")
+STEP_KERNEL_SOURCES = ("lb_cfg.h", "lb_kernels.cuh", "lb_f32.cu", "lb_f64.cu", "lb_f32h.cu", "lb_df.cuh", "lb_df64.cu")
 
 
 def _kernel_hash():
