@@ -264,9 +264,10 @@ int lb_batch_init(lb_batch** b, const lb_params* reps, int n, const uint8_t* con
 
 /* Advance every replica by n >= 0 steps, asynchronously.  Schedule 0: CUDA-graph replay of one
  * launch per step over all (replica, tile) items.  Schedule 1: cooperative persistent launches of
- * steps_per_launch steps each (graph-captured when the driver allows it), with bounded waits on
- * neighbour-tile step counters; a wait that runs out is reported as LB_ETIMEOUT by the next
- * lb_batch_sync / lb_batch_observables / lb_batch_get_*, and the state is then invalid. */
+ * steps_per_launch steps each (graph-captured when the driver allows it); between steps every CTA
+ * meets the others at a grid-wide barrier whose waits are bounded; a wait that runs out is reported
+ * as LB_ETIMEOUT by the next lb_batch_sync / lb_batch_observables / lb_batch_get_*, and the state is
+ * then invalid. */
 int lb_batch_step(lb_batch* b, int n);
 
 /* Choose the schedule (0 per-step, 1 persistent), the tile candidate and the steps per persistent
@@ -296,9 +297,9 @@ int lb_batch_stress(lb_batch* b, int replica, double* out4, double* row, double*
 int lb_batch_sync(lb_batch* b);
 
 /* Test hook for failure detection: sets the SM-clock budget of every persistent wait (default 4e9
- * cycles, about 2 s) and, when withhold_item >= 0, makes the persistent kernel never publish that
- * work item's step counter, so its neighbours' bounded waits run out and the launch ends with
- * LB_ETIMEOUT instead of hanging. */
+ * cycles, about 2 s) and, when withhold_item >= 0, makes CTA number withhold_item (modulo the
+ * persistent grid) leave before the first step barrier, so the other CTAs' bounded waits run out and
+ * the launch ends with LB_ETIMEOUT instead of hanging. */
 int lb_batch_set_wait_budget(lb_batch* b, long long cycles, int withhold_item);
 
 void lb_batch_destroy(lb_batch* b);

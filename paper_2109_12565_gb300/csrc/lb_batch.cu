@@ -7,18 +7,19 @@
 //   0  per-step: one launch per time step over all items (grid = items),
 //      replayed from a CUDA graph of kBatchGraphLen steps;
 //   1  persistent: one cooperative launch of co-resident CTAs runs K steps;
-//      CTA b owns items b, b + G, b + 2G, ... and processes them in step
-//      order.  Each item publishes "steps done" in a counter (st.release);
-//      before step s an item waits (ld.acquire, bounded by a clock budget;
-//      eight lanes of the second warp watch the eight neighbours at once,
-//      while thread 0 publishes the previous item: a barrier, then one
-//      st.release, which is cumulative over the barrier)
-//      until its 8 neighbour tiles have done s steps, which orders every read
-//      of step s after the neighbours' writes of step s - 1 and every write of
-//      step s after their reads of step s - 1.  Loads bypass L1 (ld.global.cg)
-//      because the launch rewrites the buffers it reads.  A wait that runs out
-//      sets an error word; every CTA then leaves, and the host reports
-//      LB_ETIMEOUT.
+//      CTA b owns items b, b + G, b + 2G, ... and runs them back to back,
+//      then meets every other CTA at a grid-wide barrier before the next
+//      step.  The barrier is a generation counter: each CTA reads the
+//      generation, arrives with one atom.add.acq_rel on the arrival count
+//      (after a CTA barrier, so the release covers all its threads' stores),
+//      and the last arriver resets the count and releases the next
+//      generation, which the others wait for with ld.acquire, bounded by a
+//      clock budget.  The barrier orders every read of a buffer after all
+//      of the previous step's writes to it and every write after all of the
+//      previous step's reads, so the step's loads may go through L1: no
+//      load of a buffer is in flight across the barrier that orders its
+//      writes.  A wait that runs out sets an error word; every CTA then
+//      leaves, and the host reports LB_ETIMEOUT.
 // The schedule and the tile shape are picked by lb_batch_autotune.
 #include <cuda_runtime.h>
 
@@ -66,68 +67,75 @@ lb_batch_step_kernel(const ReplicaDesc<S>* __restrict__ reps, const int4* __rest
                                                        nullptr, acc);
 }
 
+__device__ __forceinline__ int atom_add_acq_rel_gpu(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void st_relaxed_gpu(int* p, int v) {
+  asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier of a cooperative launch (bar[0] arrivals, bar[1] generation); false when a wait ran
+// out or another CTA reported one (the caller then leaves).
+__device__ __forceinline__ bool grid_barrier(int* bar, int* err, long long budget, int tid) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (tid == 0) {
+    int ok = 1;
+    const int g = ld_relaxed_gpu(bar + 1);
+    if (atom_add_acq_rel_gpu(bar, 1) == (int)gridDim.x - 1) {
+      st_relaxed_gpu(bar, 0);
+      st_release_gpu(bar + 1, g + 1);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire_gpu(bar + 1) == g) {
+        if (ld_relaxed_gpu(err) != 0) {
+          ok = 0;
+          break;
+        }
+        if (clock64() - t0 > budget) {
+          atomicCAS(err, 0, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 template <class S, bool SHIFT, int TX, int TY, int BY, int MB>
 __global__ void __launch_bounds__(TX * BY, MB)
-lb_batch_persistent_kernel(const ReplicaDesc<S>* __restrict__ reps, const int4* __restrict__ items,
-                           const int* __restrict__ nbrs, int* counters, int* err, int n_items, int parity0,
-                           int n_steps, long long budget, int withhold) {
+lb_batch_persistent_kernel(const ReplicaDesc<S>* __restrict__ reps, const int4* __restrict__ items, int* bar, int* err,
+                           int n_items, int parity0, int n_steps, long long budget, int withhold) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto& sm = *reinterpret_cast<TileSmem<S, TX, TY, false>*>(smem_raw);
-  __shared__ int s_go;
   const int tid = threadIdx.y * TX + threadIdx.x;
+  // failure-detection hook: CTA `withhold` (mod the grid) leaves before the first step barrier
+  const bool withheld = withhold >= 0 && withhold % (int)gridDim.x == (int)blockIdx.x;
   double acc[kObsSlots];
   for (int s = 0; s < n_steps; ++s) {
     const int parity = (parity0 + s) & 1;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
       const int4 it = items[item];
-      if (tid >= 32 && tid < 64) {
-        // warp 1: lanes 0-7 each watch one neighbour's counter, so one round trip covers all eight;
-        // meanwhile thread 0 (warp 0) may still be publishing the previous item
-        const int lane = tid - 32;
-        int ok = lane == 0 ? (ld_relaxed_gpu(err) == 0) : 1;
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (ok && s > 0) {
-          const int nb = lane < 8 ? nbrs[item * 8 + lane] : -1;
-          bool ready = nb < 0;
-          const long long t0 = clock64();
-          for (;;) {
-            if (!ready) ready = ld_acquire_gpu(counters + nb) >= s;
-            if (__all_sync(0xffffffffu, ready)) break;
-            int stop = 0;
-            if (lane == 0) {
-              if (ld_relaxed_gpu(err) != 0) {
-                stop = 1;
-              } else if (clock64() - t0 > budget) {
-                atomicCAS(err, 0, 1);
-                stop = 1;
-              }
-            }
-            if (__shfl_sync(0xffffffffu, stop, 0)) {
-              ok = 0;
-              break;
-            }
-            __nanosleep(64);
-          }
-        }
-        if (lane == 0) s_go = ok;
-      }
-      __syncthreads();
-      if (!s_go) return;
       const ReplicaDesc<S>& rd = reps[it.x];
-      tile_step<S, S, SHIFT, MODE_STEP, TX, TY, BY, true>(rd.buf[parity], rd.buf[parity ^ 1], rd.kp, it.y, it.z, sm,
-                                                          nullptr, acc);
-      // every thread's stores of this item come before the barrier; the release by thread 0 is cumulative
-      // over it, so a neighbour that acquires the counter sees all of them
-      __syncthreads();
-      if (tid == 0 && item != withhold) st_release_gpu(counters + item, s + 1);
+      tile_step<S, S, SHIFT, MODE_STEP, TX, TY, BY>(rd.buf[parity], rd.buf[parity ^ 1], rd.kp, it.y, it.z, sm, nullptr,
+                                                    acc);
+      __syncthreads();  // the next item's phase A rewrites the shared memory
     }
+    if (s + 1 == n_steps) break;  // the launch boundary orders the last step
+    if (withheld) return;
+    if (!grid_barrier(bar, err, budget, tid)) return;
   }
 }
 
 struct BatchArgs {
   const void* reps;
   const int4* items;
-  const int* nbrs;
   int* counters;
   int* err;
   int n_items;
@@ -174,7 +182,7 @@ template <class S, bool SHIFT, int TX, int TY, int BY, int MB> struct BatchKerne
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, static_cast<const ReplicaDesc<S>*>(a.reps), a.items, a.nbrs, a.counters, a.err,
+    return cudaLaunchKernelEx(&cfg, k, static_cast<const ReplicaDesc<S>*>(a.reps), a.items, a.counters, a.err,
                               a.n_items, a.parity, a.n_steps, a.budget, a.withhold);
   }
 };
@@ -228,7 +236,7 @@ struct lb_batch {
   std::vector<size_t> base;
   std::vector<StepCfg> cfg;
   unsigned char* ws = nullptr;
-  size_t reps_off = 0, items_off = 0, nbrs_off = 0, counters_off = 0, err_off = 0;
+  size_t reps_off = 0, items_off = 0, counters_off = 0, err_off = 0;
   int max_items = 0, n_items = 0;
   int schedule = 0, tile = 0, steps_per_launch = 64, grid = 0;
   int parity = 0;
@@ -266,7 +274,7 @@ size_t desc_bytes(int precision) {
 
 // Offsets of every replica and of the batch tables.
 size_t batch_layout(const lb_params* reps, int n, const int* has_mask, std::vector<Layout>* L, std::vector<size_t>* base,
-                    size_t* reps_off, size_t* items_off, size_t* nbrs_off, size_t* counters_off, size_t* err_off,
+                    size_t* reps_off, size_t* items_off, size_t* counters_off, size_t* err_off,
                     int* max_items) {
   size_t off = 0;
   int items = 0;
@@ -281,17 +289,15 @@ size_t batch_layout(const lb_params* reps, int n, const int* has_mask, std::vect
   off += round_up((size_t)n * desc_bytes(reps[0].precision), kAlign);
   *items_off = off;
   off += round_up((size_t)items * sizeof(int4), kAlign);
-  *nbrs_off = off;
-  off += round_up((size_t)items * 8 * sizeof(int), kAlign);
-  *counters_off = off;
-  off += round_up((size_t)items * sizeof(int), kAlign);
+  *counters_off = off;  // persistent schedule: step barrier (arrivals, generation)
+  off += kAlign;
   *err_off = off;
   off += kAlign;
   *max_items = items;
   return off;
 }
 
-// Work list and neighbour table for tile candidate k; uploads them and sizes the persistent grid.
+// Work list for tile candidate k; uploads it and sizes the persistent grid.
 int configure(lb_batch* b, int schedule, int tile, int steps_per_launch) {
   int nc = 0;
   const BatchCand* cs = cands(b->precision, &nc);
@@ -300,28 +306,15 @@ int configure(lb_batch* b, int schedule, int tile, int steps_per_launch) {
   if (steps_per_launch < 2 || (steps_per_launch & 1)) return bfail(b, LB_EINVAL, "steps_per_launch must be even, >= 2");
   const TileChoice t = cs[tile].t;
   std::vector<int4> items;
-  std::vector<int> nbrs;
   for (int r = 0; r < b->n; ++r) {
     const lb_params& p = b->p[r];
     const int ntx = (p.nx + t.tx - 1) / t.tx, nty = (p.ny + t.ty - 1) / t.ty;
-    const int first = (int)items.size();
     for (int ty = 0; ty < nty; ++ty)
-      for (int tx = 0; tx < ntx; ++tx) {
-        items.push_back(make_int4(r, tx * t.tx, ty * t.ty, 0));
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            if (dx == 0 && dy == 0) continue;
-            const int nx_ = ((tx + dx) % ntx + ntx) % ntx;
-            int ny_ = ty + dy;
-            if (p.periodic_y) ny_ = (ny_ % nty + nty) % nty;
-            nbrs.push_back((ny_ < 0 || ny_ >= nty) ? -1 : first + ny_ * ntx + nx_);
-          }
-      }
+      for (int tx = 0; tx < ntx; ++tx) items.push_back(make_int4(r, tx * t.tx, ty * t.ty, 0));
   }
   if ((int)items.size() > b->max_items) return bfail(b, LB_EINVAL, "work list larger than its table");
   BCUDA(b, cudaStreamSynchronize(b->stream));
   BCUDA(b, cudaMemcpy(b->ws + b->items_off, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
-  BCUDA(b, cudaMemcpy(b->ws + b->nbrs_off, nbrs.data(), nbrs.size() * sizeof(int), cudaMemcpyHostToDevice));
   int occ = 0, dev = 0, sms = 0;
   BCUDA(b, cs[tile].occupancy(&occ));
   BCUDA(b, cudaGetDevice(&dev));
@@ -344,7 +337,6 @@ BatchArgs args_for(const lb_batch* b, int parity, int n_steps) {
   BatchArgs a;
   a.reps = b->ws + b->reps_off;
   a.items = reinterpret_cast<const int4*>(b->ws + b->items_off);
-  a.nbrs = reinterpret_cast<const int*>(b->ws + b->nbrs_off);
   a.counters = reinterpret_cast<int*>(b->ws + b->counters_off);
   a.err = reinterpret_cast<int*>(b->ws + b->err_off);
   a.n_items = b->n_items;
@@ -366,7 +358,7 @@ cudaError_t enqueue(const lb_batch* b, int parity, int steps, cudaStream_t s) {
     }
     return cudaSuccess;
   }
-  cudaError_t e = cudaMemsetAsync(b->ws + b->counters_off, 0, (size_t)b->n_items * sizeof(int), s);
+  cudaError_t e = cudaMemsetAsync(b->ws + b->counters_off, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   return c.persistent(args_for(b, parity, steps), b->grid, s);
 }
@@ -413,7 +405,7 @@ int check_err_word(lb_batch* b) {
   int v = 0;
   BCUDA(b, cudaMemcpyAsync(&v, b->ws + b->err_off, sizeof v, cudaMemcpyDeviceToHost, b->stream));
   BCUDA(b, cudaStreamSynchronize(b->stream));
-  if (v != 0) return bfail(b, LB_ETIMEOUT, "a persistent-kernel wait for a neighbour tile ran out; the state is invalid");
+  if (v != 0) return bfail(b, LB_ETIMEOUT, "a persistent-kernel wait at the step barrier ran out; the state is invalid");
   return LB_OK;
 }
 
@@ -429,9 +421,9 @@ int lb_batch_workspace_size(const lb_params* reps, int n, const int* has_mask, s
     if (reps[r].precision == LB_FP32_FP16T || reps[r].precision == LB_DF64)
       return bfail(nullptr, LB_EINVAL, "batched ensembles store LB_FP64 or LB_FP32_SHIFTED");
   }
-  size_t a, c, d, e, f;
+  size_t a, c, e, f;
   int m;
-  *bytes = batch_layout(reps, n, has_mask, nullptr, nullptr, &a, &c, &d, &e, &f, &m);
+  *bytes = batch_layout(reps, n, has_mask, nullptr, nullptr, &a, &c, &e, &f, &m);
   return LB_OK;
 }
 
@@ -457,7 +449,7 @@ int lb_batch_init(lb_batch** out, const lb_params* reps, int n, const uint8_t* c
   b->precision = reps[0].precision;
   b->p.assign(reps, reps + n);
   const size_t total = batch_layout(reps, n, has_mask.data(), &b->L, &b->base, &b->reps_off, &b->items_off,
-                                    &b->nbrs_off, &b->counters_off, &b->err_off, &b->max_items);
+                                    &b->counters_off, &b->err_off, &b->max_items);
   auto bail = [&](int code) {
     std::snprintf(g_batch_err, sizeof g_batch_err, "%s", b->err);
     lb_batch_destroy(b);
