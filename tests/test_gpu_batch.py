@@ -90,8 +90,8 @@ def test_batch_autotune_advances_consistently():
 
 
 def test_persistent_wait_timeout_is_reported_not_hung():
-    """Failure detection: item 0 never publishes its step counter; its neighbours' waits run out after
-    ~1e6 SM cycles, the kernel leaves and the host sees LB_ETIMEOUT."""
+    """Failure detection: CTA 0 of the persistent kernel leaves before the first step barrier; the other
+    CTAs' waits there run out after ~1e6 SM cycles, the kernel ends and the host sees LB_ETIMEOUT."""
     params, r1, r2, T0, masks = _replicas()
     b = lb.Batch(params, r1, r2, T0, masks=masks, precision=lb.LB_FP32_SHIFTED)
     b.configure(1, 0, 4)
