@@ -8,7 +8,7 @@
 namespace tlb {
 
 // MODE_STEP_NU: a step that also sums u^(H)_y T over the fluid nodes of its input state, one partial
-// per CTA (the Nusselt number's advective part, Eq. NuTime), for the adjoint's forward pass.
+// per warp (the Nusselt number's advective part, Eq. NuTime), for the adjoint's forward pass.
 enum Mode : int { MODE_STEP = 0, MODE_OBS = 1, MODE_FIELDS = 2, MODE_STEP_NU = 3 };
 __host__ __device__ constexpr bool mode_needs_T(int m) { return m == MODE_OBS || m == MODE_FIELDS; }
 __host__ __device__ constexpr bool mode_steps(int m) { return m == MODE_STEP || m == MODE_STEP_NU; }
@@ -99,7 +99,7 @@ inline cudaError_t launch_mode(int precision, int mode, const StepCfg& c, const 
     default: return launch_df64(mode, c, fin, fout, aux, s);
   }
 }
-// Double-float exp tables of the LB_DF64 form on the current device (once per device, before capture).
+// Double-float exp tables of the LB_DF64 form, written to the current device (lb_init, before capture).
 cudaError_t df_exp_tables_init();
 // Error codes a kernel writes to StepCfg::err (the host maps them to LB_ETIMEOUT).
 constexpr int kErrWaitTimeout = 1;
@@ -116,8 +116,9 @@ cudaError_t stress_run(const StepCfg& cfg, int precision, const void* cur, doubl
                        double** d_rows, double** d_tot);
 cudaError_t stress_fetch(int nx, int ny, const double* stage, const double* d_rows, const double* d_tot, double* out4,
                          double* row, double* field, cudaStream_t s);
-// A step (MODE_STEP_NU) from fin to fout that also writes, per CTA, the sum of u^(H)_y T over the fluid
-// nodes of fin (step_nu_blocks partials, in CTA order); one fixed tile shape per precision.
+// A step (MODE_STEP_NU) from fin to fout that also writes, per warp, the sum of u^(H)_y T over the fluid
+// nodes of fin in the arithmetic precision (step_nu_blocks partials, in CTA and warp order); one fixed
+// tile shape per precision.
 int step_nu_blocks(int precision, int nx, int ny);
 cudaError_t launch_step_nu_f64(const StepCfg& c, const void* fin, void* fout, double* partials, cudaStream_t s);
 cudaError_t launch_step_nu_f32(const StepCfg& c, const void* fin, void* fout, double* partials, cudaStream_t s);

@@ -2,37 +2,27 @@
 // (8 bytes, the footprint of FP64), every operation in double-float arithmetic on the FP32 pipe
 // (lb_df.cuh); results stay within the FP64 form's tolerance against the FP64 oracle.
 #include <cmath>
-#include <mutex>
 
 #include "lb_df.cuh"
 
 namespace tlb {
 
 namespace {
-std::mutex g_tab_mu;
-unsigned long long g_tab_done = 0;  // one bit per device ordinal (mod 64)
-
 float2 split(double v) {
   const float h = (float)v;
   return make_float2(h, (float)(v - (double)h));
 }
 }  // namespace
 
-// exp(-k / 64) and exp(-j / 4096) as double-float roundings of the FP64 library values, written once
-// per device (before any stream capture: lb_init calls it).
+// exp(-k / 64) and exp(-j / 4096) as double-float roundings of the FP64 library values, written to the
+// current device by every lb_init of an LB_DF64 lattice (2.6 KB, before any stream capture); nothing is
+// remembered between calls, so a device reset in between does no harm.
 cudaError_t df_exp_tables_init() {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  std::lock_guard<std::mutex> lock(g_tab_mu);
-  const unsigned long long bit = 1ull << (dev & 63);
-  if (g_tab_done & bit) return cudaSuccess;
   float2 t1[kDfExpT1], t2[kDfExpT2];
   for (int k = 0; k < kDfExpT1; ++k) t1[k] = split(std::exp(-(double)k / 64.0));
   for (int j = 0; j < kDfExpT2; ++j) t2[j] = split(std::exp(-(double)j / 4096.0));
-  e = cudaMemcpyToSymbol(g_df_exp_t1, t1, sizeof t1);
+  cudaError_t e = cudaMemcpyToSymbol(g_df_exp_t1, t1, sizeof t1);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_df_exp_t2, t2, sizeof t2);
-  if (e == cudaSuccess) g_tab_done |= bit;
   return e;
 }
 

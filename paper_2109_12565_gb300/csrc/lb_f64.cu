@@ -36,9 +36,9 @@ cudaError_t launch_step_nu_f64(const StepCfg& c, const void* fin, void* fout, do
                                                                       partials, s);
 }
 
-int step_nu_blocks(int precision, int nx, int ny) {
+int step_nu_blocks(int precision, int nx, int ny) {  // partials: CTAs x 8 warps (256 threads)
   const dim3 g = precision == LB_FP64 ? grid_for(nx, ny, 32, 16) : grid_for(nx, ny, 32, 8);
-  return (int)(g.x * g.y);
+  return (int)(g.x * g.y) * 8;
 }
 
 cudaError_t init_f64(const StepCfg& c, const double* fields, void* buf, cudaStream_t s) {

@@ -793,7 +793,7 @@ __device__ __forceinline__ C step_finish(SF<S>* __restrict__ fout, const KParams
 template <class S, class C, bool SHIFT, int MODE, bool FAST, int TX, int TY, int BY, class Src>
 __device__ __forceinline__ void tile_phase_b(const Src& pop, SF<S>* __restrict__ fout, const KParams<C>& kp, int x0, int y0,
                                              const TileSmem<C, TX, TY, mode_needs_T(MODE)>& sm, double* __restrict__ aux,
-                                             double acc[kObsSlots]) {
+                                             double acc[kObsSlots], C* nu = nullptr) {
   const int nx = kp.nx, ny = kp.ny, pitch = kp.pitch, plane = kp.plane;
 #pragma unroll 1
   for (int k = 0; k < TY / BY; ++k) {
@@ -832,7 +832,7 @@ __device__ __forceinline__ void tile_phase_b(const Src& pop, SF<S>* __restrict__
     node_force_pair<C>(sm, kp, cx, cy, v2<C>(r1, r2), fx2, fyp2, q0, q1, q2, q3, q4);
     if constexpr (mode_steps(MODE)) {
       const C uyT = step_finish<S, C, SHIFT, FAST>(fout, kp, sm, f, h, g, m, tx, ty, gx, gy, idx, fx2, fyp2);
-      if constexpr (MODE == MODE_STEP_NU) acc[0] += (double)uyT;  // as MODE_OBS accumulates it
+      if constexpr (MODE == MODE_STEP_NU) *nu = s_add(*nu, uyT);  // in the arithmetic precision
       continue;
     }
     const V2<C> fy2 = buoyant_fy<C>(kp, fyp2, v2<C>(r1, r2), T);
@@ -889,18 +889,18 @@ __device__ __forceinline__ void tile_phase_b(const Src& pop, SF<S>* __restrict__
 template <class S, class C, bool SHIFT, int MODE, int TX, int TY, int BY, bool CG = false>
 __device__ __forceinline__ void tile_step(const SF<S>* __restrict__ fin, SF<S>* __restrict__ fout, const KParams<C>& kp,
                                           int x0, int y0, TileSmem<C, TX, TY, mode_needs_T(MODE)>& sm,
-                                          double* __restrict__ aux, double acc[kObsSlots]) {
+                                          double* __restrict__ aux, double acc[kObsSlots], C* nu = nullptr) {
   constexpr int NT = TX * BY;
   const int tid = threadIdx.y * TX + threadIdx.x;
   const bool fast = tile_phase_a<S, C, SHIFT, mode_needs_T(MODE), TX, TY, NT, CG>(fin, kp, x0, y0, sm, tid);
   const GlobalPopSource<S, CG> pop{fin, kp.plane};
   if constexpr (Storage<S>::kFastPath) {
     if (mode_steps(MODE) && fast) {
-      tile_phase_b<S, C, SHIFT, MODE, true, TX, TY, BY>(pop, fout, kp, x0, y0, sm, aux, acc);
+      tile_phase_b<S, C, SHIFT, MODE, true, TX, TY, BY>(pop, fout, kp, x0, y0, sm, aux, acc, nu);
       return;
     }
   }
-  tile_phase_b<S, C, SHIFT, MODE, false, TX, TY, BY>(pop, fout, kp, x0, y0, sm, aux, acc);
+  tile_phase_b<S, C, SHIFT, MODE, false, TX, TY, BY>(pop, fout, kp, x0, y0, sm, aux, acc, nu);
 }
 
 // Block-wide deterministic sum of the observable accumulators into aux[slot * kObsSlots + v].
@@ -922,20 +922,13 @@ __device__ __forceinline__ void block_obs_store(double acc[kObsSlots], double* _
   }
 }
 
-// Block-wide deterministic sum of one value per thread into aux[slot].
-template <int NT>
-__device__ __forceinline__ void block_sum_store(double v, double* __restrict__ aux, long long slot) {
-  __shared__ double s_red1[NT / 32];
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const double s = warp_sum(v);
-  if ((tid & 31) == 0) s_red1[tid >> 5] = s;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < NT / 32; ++w) t += s_red1[w];
-    aux[slot] = t;
-  }
+// Warp sum in the arithmetic precision (a fixed shuffle tree).
+__device__ __forceinline__ float warp_sum_c(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
 }
+__device__ __forceinline__ double warp_sum_c(double v) { return warp_sum(v); }
 
 template <class S, class C, bool SHIFT, int MODE, int TX, int TY, int BY, int MINB>
 __global__ void __launch_bounds__(TX * BY, MINB)
@@ -945,9 +938,16 @@ lb_step_kernel(const SF<S>* __restrict__ fin, SF<S>* __restrict__ fout, const KP
   double acc[kObsSlots];
 #pragma unroll
   for (int v = 0; v < kObsSlots; ++v) acc[v] = 0.0;
-  tile_step<S, C, SHIFT, MODE, TX, TY, BY>(fin, fout, kp, blockIdx.x * TX, blockIdx.y * TY, sm, aux, acc);
+  C nu = C(0);
+  tile_step<S, C, SHIFT, MODE, TX, TY, BY>(fin, fout, kp, blockIdx.x * TX, blockIdx.y * TY, sm, aux, acc, &nu);
   if constexpr (MODE == MODE_OBS) block_obs_store<TX * BY>(acc, aux, (long long)blockIdx.y * gridDim.x + blockIdx.x);
-  if constexpr (MODE == MODE_STEP_NU) block_sum_store<TX * BY>(acc[0], aux, (long long)blockIdx.y * gridDim.x + blockIdx.x);
+  if constexpr (MODE == MODE_STEP_NU) {
+    // one partial per warp, no CTA barrier: aux[(CTA) * warps + warp]
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const C v = warp_sum_c(nu);
+    if ((tid & 31) == 0)
+      aux[((long long)blockIdx.y * gridDim.x + blockIdx.x) * (TX * BY / 32) + (tid >> 5)] = (double)v;
+  }
 }
 
 // Rest equilibria f = w_i rho, g = w_i T at fluid nodes (stored minus the shift), 0 at solid nodes.
