@@ -112,18 +112,7 @@ void drop_graphs(lb_handle* h) {
 
 void fill_cfg(lb_handle* h, const uint8_t* d_mask) {
   h->cfg = make_stepcfg(h->p, h->L.pitch, d_mask);
-  h->cfg.err = reinterpret_cast<int*>(h->ws + h->L.err_off);
 }
-
-// LB_ETIMEOUT when a kernel with bounded waits gave up (the state is then invalid).
-int check_err_word(lb_handle* h) {
-  int v = 0;
-  CUDA_TRY(h, cudaMemcpyAsync(&v, h->cfg.err, sizeof v, cudaMemcpyDeviceToHost, h->stream));
-  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  if (v != 0) return fail(h, LB_ETIMEOUT, "a bounded device wait ran out; the state is invalid");
-  return LB_OK;
-}
-
 
 int build_graph(lb_handle* h, int parity) {
   cudaGraph_t g = nullptr;
@@ -245,7 +234,6 @@ int lb_step(lb_handle* h, int n) {
 
 int lb_observables(lb_handle* h, lb_obs* out) {
   if (!h || !out) return fail(h, LB_EINVAL, "handle and out are required");
-  if (int rc = check_err_word(h)) return rc;
   double* part = reinterpret_cast<double*>(h->ws + h->L.part_off);
   double* dobs = reinterpret_cast<double*>(h->ws + h->L.obs_off);
   CUDA_TRY(h, launch(h, MODE_OBS, h->buf[h->cur], nullptr, part, h->stream));
@@ -436,7 +424,7 @@ int lb_sync(lb_handle* h) {
   if (!h) return fail(nullptr, LB_EINVAL, "handle is NULL");
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   CUDA_TRY(h, cudaGetLastError());
-  return check_err_word(h);
+  return LB_OK;
 }
 
 void lb_destroy(lb_handle* h) {

@@ -38,7 +38,6 @@ struct StepCfg {
   double kappa;               // (tau_g - 1/2) / 3, Eq. K
   double H;                   // wall-to-wall height ny - 2
   double u_wall[2];           // x velocity of the bottom / top flat wall rows (Couette)
-  int* err;                   // device error word for bounded waits (nullptr: kernels that wait are not used)
 };
 
 // Tile shapes (nodes per CTA in x and y; threads per CTA = TX * BY).
@@ -101,8 +100,6 @@ inline cudaError_t launch_mode(int precision, int mode, const StepCfg& c, const 
 }
 // Double-float exp tables of the LB_DF64 form, written to the current device (lb_init, before capture).
 cudaError_t df_exp_tables_init();
-// Error codes a kernel writes to StepCfg::err (the host maps them to LB_ETIMEOUT).
-constexpr int kErrWaitTimeout = 1;
 // Total shear stress (lb_stress.cu): the field mode writes rho_1, rho_2, T, u^(H) (5 planes of nx*ny
 // doubles) to `stage`, then sigma_xy (1 plane), per-row partials, row sums and totals follow there;
 // stress_staging_doubles is the staging it needs.  stress_fetch copies the means (out4), the per-row

@@ -19,7 +19,7 @@ inline size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // final observable vector.  Offsets are relative to the lattice's base address.
 struct Layout {
   int pitch = 0;
-  size_t elem = 0, buf_bytes = 0, mask_off = 0, part_off = 0, obs_off = 0, err_off = 0, total = 0;
+  size_t elem = 0, buf_bytes = 0, mask_off = 0, part_off = 0, obs_off = 0, total = 0;
   int n_blocks = 0;
 };
 
@@ -74,8 +74,6 @@ inline Layout layout_for(const lb_params* p, int has_mask) {
   off += round_up((size_t)L.n_blocks * kObsSlots * sizeof(double), kAlign);
   L.obs_off = off;
   off += round_up(kObsOut * sizeof(double), kAlign);
-  L.err_off = off;  // error word of kernels with bounded waits
-  off += kAlign;
   L.total = off;
   return L;
 }
