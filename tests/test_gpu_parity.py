@@ -421,3 +421,25 @@ def test_fresh_handle_reports_no_error_on_reused_memory():
     g.step(2)
     g.sync()
     assert g.observables()["status"] == lb.LB_OK
+
+
+def test_df64_state_roundtrip_and_rejections():
+    """LB_DF64: lb_set_state splits each FP64 population into a double-float pair and lb_get_state
+    adds the pair back, so a round trip loses at most 2^-48 relative; batches and the adjoint, which
+    exist for FP64 and FP32-shifted storage, reject the form."""
+    w = I.emulsion_small()
+    o = O.Oracle(w.params, w.rho1, w.rho2, w.T0)
+    o.step(30)
+    g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, precision=lb.LB_DF64)
+    g.set_state(o.state)
+    back = g.get_state()
+    assert np.abs(back - o.state).max() <= 2.0 ** -48 * np.abs(o.state).max()
+    g.step(40)
+    o.step(40)
+    assert np.abs(g.get_state() - o.state).max() <= 1e-11
+    with pytest.raises(lb.LbError) as e:
+        g.adjoint(4)
+    assert e.value.code == lb.LB_EINVAL
+    with pytest.raises(lb.LbError) as e:
+        lb.Batch([w.params], [w.rho1], [w.rho2], [w.T0], precision=lb.LB_DF64)
+    assert e.value.code == lb.LB_EINVAL
