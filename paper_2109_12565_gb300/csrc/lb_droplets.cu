@@ -13,16 +13,19 @@
 //   D6  links: 2 x 2 windows with three colours give the three pairs, with four colours the four
 //       pairs of neighbouring corners.
 //
-// Pipeline (all on the caller's stream, no host round trip until the counts are read):
-//   fields (MODE_FIELDS of the step kernel) -> labels: union-find with atomicMin hooks, so every
-//   root ends as its component's smallest node -> ids: exclusive block scan of the root flags ->
-//   centres: 64-bit integer sums of the unwrapped offsets (exact, order independent) -> cell
-//   grid of the centres -> colours: nearest centre by rings of cells with an exact stopping
-//   distance -> links: a bounded adjacency set per droplet (atomicCAS), sorted per droplet,
+// Pipeline (all on the caller's stream, no host round trip until the counts are read; the
+// per-droplet kernels take the droplet count from the workspace header the labelling wrote):
+//   fields (MODE_FIELDS of the step kernel) -> reset of the accumulators -> labels: union-find with
+//   atomicMin hooks, so every root ends as its component's smallest node, first inside 32 x 32 tiles
+//   in shared memory, then across the tile borders -> ids: block scan of the root flags -> centres:
+//   64-bit integer sums of the unwrapped offsets (exact, order independent) -> cell grid of the
+//   centres -> colours: nearest staged centre, screened in FP32 and settled in FP64 near Voronoi
+//   edges -> links: a bounded adjacency set per droplet (atomicCAS), sorted per droplet in a warp,
 //   compacted by a scan.  Every result is independent of thread scheduling.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <cstdio>
 #include <vector>
 
@@ -37,6 +40,7 @@ constexpr int kCell = 32;       // target edge of a centre-grid cell (nodes): ab
 constexpr int kErrDegree = 1;   // a droplet has more than kMaxDeg links
 constexpr int kErrDrops = 2;    // more droplets than max_drops
 constexpr int kErrUnion = 4;    // a union-find loop ran past its bound
+constexpr unsigned kGridCap = 4 * 152;  // blocks of the grid-stride kernels (4 per SM of a GB300)
 
 // Header at the start of the workspace (device-written counts, host-written sizes).
 struct Header {
@@ -226,174 +230,284 @@ cudaError_t exclusive_scan(const int* in, long long n, int* out, int* bsum, cuda
 }
 
 // ---------------------------------------------------------------- labels (D1-D3)
+//
+// Union-find with every root the smallest node of its set (a hook points the larger root at the
+// smaller one), in two levels: each CTA labels a 32 x 32 tile in shared memory (label_local), so
+// only the edges that cross a tile border, or the periodic seams, are united in global memory
+// (label_border); the parent chains left there run between tile-local roots and stay short.
+constexpr int kLT = 32;           // label tile edge
+constexpr int kLThreads = 256;
 
-__global__ void label_init(const double* __restrict__ rho1, double threshold, Geo g, int* __restrict__ lab) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= (long long)g.nx * g.ny) return;
-  const int x = (int)(n % g.nx), y = (int)(n / g.nx);
-  lab[n] = (!is_solid(g, x, y) && rho1[n] > threshold) ? (int)n : -1;
-}
-
-__device__ __forceinline__ int find_root(const int* lab, int a) {
+// Root of a, following parents; -1 if the chain is broken or longer than the bound.
+__device__ __forceinline__ int find_root(const int* lab, int a, int bound) {
   int r = a;
-  for (int k = 0; k < (1 << 26); ++k) {  // bounded: a parent chain is shorter than the lattice
+  for (int k = 0; k < bound; ++k) {
     const int p = lab[r];
     if (p == r) return r;
+    if (p < 0) return -1;
     r = p;
   }
   return -1;
 }
 
-// Hook the larger root under the smaller one until both nodes share a root.
-__device__ __forceinline__ void unite(int* lab, int a, int b, int* err) {
-  for (int k = 0; k < (1 << 20); ++k) {
-    a = find_root(lab, a);
-    b = find_root(lab, b);
-    if (a < 0 || b < 0) break;
-    if (a == b) return;
+// Hook the larger root under the smaller one until a and b share a root (lab in global or shared
+// memory); false when a loop ran past its bound.
+__device__ __forceinline__ bool unite(int* lab, int a, int b, int bound) {
+  for (int k = 0; k < bound; ++k) {
+    a = find_root(lab, a, bound);
+    b = find_root(lab, b, bound);
+    if (a < 0 || b < 0) return false;
+    if (a == b) return true;
     if (a < b) {
       const int t = a;
       a = b;
       b = t;
     }
     const int old = atomicMin(&lab[a], b);
-    if (old == a) return;  // a was still a root: hooked
-    a = old;               // a was hooked meanwhile; continue from its new parent
+    if (old == a) return true;  // a was still a root: hooked
+    a = old;                    // a was hooked meanwhile; continue from its new parent
   }
-  atomicOr(err, kErrUnion);
+  return false;
 }
 
-__global__ void label_merge(Geo g, int* lab, int* err) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= (long long)g.nx * g.ny || lab[n] < 0) return;
-  const int x = (int)(n % g.nx), y = (int)(n / g.nx);
-  const int xr = x + 1 == g.nx ? 0 : x + 1;
-  const long long right = (long long)y * g.nx + xr;
-  if (right != n && lab[right] >= 0) unite(lab, (int)n, (int)right, err);
-  int yu = y + 1;
-  if (yu == g.ny) yu = g.periodic_y ? 0 : -1;
-  if (yu >= 0) {
-    const long long up = (long long)yu * g.nx + x;
-    if (up != n && lab[up] >= 0) unite(lab, (int)n, (int)up, err);
+// One CTA per 32 x 32 tile, one warp per row of 32 nodes (a row at a time): D1 foreground and, by a
+// warp ballot, the runs of consecutive foreground nodes, each node pointing at its run's first node;
+// then one union per overlap of two runs in consecutive rows; then the global index of each node's
+// tile-local root (the tile's row-major order is the lattice's order, so the local root, the
+// smallest run start of the set, is also its smallest node in global numbering).
+__global__ void __launch_bounds__(kLThreads) label_local(const double* __restrict__ rho1, double threshold, Geo g,
+                                                         int* __restrict__ lab, int* err) {
+  static_assert(kLT == 32, "one lane per tile column");
+  __shared__ int s[kLT * kLT];
+  __shared__ unsigned s_fg[kLT];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = kLThreads / 32;
+  const int x0 = blockIdx.x * kLT, y0 = blockIdx.y * kLT, x = x0 + lane;
+  for (int ly = warp; ly < kLT; ly += nwarp) {
+    const int y = y0 + ly;
+    const bool fg = x < g.nx && y < g.ny && !is_solid(g, x, y) && rho1[y * g.nx + x] > threshold;
+    const unsigned mask = __ballot_sync(0xffffffffu, fg);
+    const unsigned starts = mask & ~(mask << 1);                            // first node of each run
+    const int start = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));  // this lane's run (if fg)
+    s[ly * kLT + lane] = fg ? ly * kLT + start : -1;
+    if (lane == 0) s_fg[ly] = mask;
+  }
+  __syncthreads();
+  bool ok = true;
+  for (int ly = warp; ly + 1 < kLT; ly += nwarp) {
+    const unsigned both = s_fg[ly] & s_fg[ly + 1];
+    if ((both & ~(both << 1)) >> lane & 1u)  // first column of an overlap of a run below and a run above
+      ok &= unite(s, ly * kLT + lane, (ly + 1) * kLT + lane, 2 * kLT * kLT);
+  }
+  if (!ok) atomicOr(err, kErrUnion);
+  __syncthreads();
+  for (int ly = warp; ly < kLT; ly += nwarp) {
+    const int y = y0 + ly;
+    if (x >= g.nx || y >= g.ny) continue;
+    const int i = ly * kLT + lane;
+    int out = -1;
+    if (s[i] >= 0) {
+      const int r = find_root(s, i, kLT * kLT);
+      out = r < 0 ? -1 : (y0 + r / kLT) * g.nx + x0 + (r & (kLT - 1));
+    }
+    lab[y * g.nx + x] = out;
   }
 }
 
-// Final labels (roots) and the root flags for the id scan (in did).
-__global__ void label_flatten(long long N, int* lab, int* __restrict__ flag) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  const int l = lab[n];
-  if (l < 0) {
-    flag[n] = 0;
+// Unions across tile borders: the right edge of each tile's last column (x + 1 wraps at nx) and the
+// upper edge of each tile's last row (y + 1 wraps when periodic_y).  Threads [0, ny * ncol) take the
+// vertical borders, the rest the horizontal ones.
+__global__ void label_border(Geo g, int ncol, int nrow, int* lab, int* err) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nv = g.ny * ncol;
+  int n, m;
+  if (t < nv) {
+    const int y = t / ncol, c = t - y * ncol;
+    const int x = min(c * kLT + kLT - 1, g.nx - 1);
+    n = y * g.nx + x;
+    m = y * g.nx + (x + 1 == g.nx ? 0 : x + 1);
+  } else if (t < nv + g.nx * nrow) {
+    const int u = t - nv, r = u / g.nx, x = u - r * g.nx;
+    const int y = min(r * kLT + kLT - 1, g.ny - 1);
+    int yu = y + 1;
+    if (yu == g.ny) {
+      if (!g.periodic_y) return;
+      yu = 0;
+    }
+    n = y * g.nx + x;
+    m = yu * g.nx + x;
+  } else {
     return;
   }
-  const int r = find_root(lab, (int)n);
-  lab[n] = r;  // every node of a chain resolves to the same root; concurrent writes store roots only
-  flag[n] = (r == (int)n) ? 1 : 0;
+  if (n == m || lab[n] < 0 || lab[m] < 0) return;
+  if (!unite(lab, n, m, 1 << 26)) atomicOr(err, kErrUnion);
 }
 
-// did[n] = id of n's droplet (the scanned position of its root), -1 for background; root table.
-__global__ void label_ids(long long N, const int* __restrict__ lab, int* did, int* __restrict__ root, int max_drops,
-                          int* err) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  const int l = lab[n];
-  if (l < 0) return;
-  // did holds the exclusive scan of the root flags; a root keeps its own entry
-  if (l == (int)n) {
-    const int id = did[n];
-    if (id < max_drops) root[id] = (int)n;
-    else atomicOr(err, kErrDrops);
+// Final labels (the roots), the root flags in flag, and per 1024-node block the number of roots
+// (the first pass of the id scan).
+__global__ void __launch_bounds__(kScanBlock) label_flatten(int N, int* lab, int* __restrict__ flag,
+                                                           int* __restrict__ bsum, int* err) {
+  __shared__ int s_warp[kScanBlock / 32];
+  const int n = blockIdx.x * kScanBlock + threadIdx.x;
+  int f = 0;
+  if (n < N) {
+    const int l = lab[n];
+    if (l >= 0) {
+      const int r = find_root(lab, n, 1 << 26);
+      if (r >= 0) {
+        lab[n] = r;  // every node of a chain resolves to the same root; concurrent writes store roots only
+        f = r == n ? 1 : 0;
+      } else {
+        atomicOr(err, kErrUnion);
+      }
+    }
+    flag[n] = f;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
+  if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = f;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int w = s_warp[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = w;
   }
 }
 
-__global__ void label_ids_spread(long long N, const int* __restrict__ lab, int* did) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  const int l = lab[n];
-  // read the root's scanned position; a non-root's own slot is read by nobody, a root writes its
-  // own value back unchanged, so the in-place update is race free
-  did[n] = l < 0 ? -1 : did[l];
+// One block: exclusive scan of in[0 .. n) into out (out may alias in); returns the total to every
+// thread.
+__device__ int block_scan_loop(const int* in, int* out, int n, int* s_warp) {
+  int carry = 0;
+  for (int base = 0; base < n; base += kScanBlock) {
+    const int i = base + threadIdx.x;
+    const int v = i < n ? in[i] : 0;
+    int total = 0;
+    const int inc = block_inclusive_scan(v, s_warp, &total);
+    if (i < n) out[i] = carry + inc - v;
+    carry += total;
+  }
+  return carry;
+}
+
+// One block: exclusive scan of the per-block root counts in place (bsum[nb] = total) and the droplet
+// count in the header (clamped to max_drops, kErrDrops beyond).
+__global__ void __launch_bounds__(kScanBlock) label_count(int* bsum, int nb, Header* h, int max_drops) {
+  __shared__ int s_warp[kScanBlock / 32];
+  const int total = block_scan_loop(bsum, bsum, nb, s_warp);
+  if (threadIdx.x == 0) {
+    bsum[nb] = total;
+    h->n_drops = total < max_drops ? total : max_drops;
+    if (total > max_drops) atomicOr(&h->err, kErrDrops);
+  }
+}
+
+// Second pass of the id scan: did[n] = number of roots before n (ids in root order, D3) and the root
+// table root[id] = node.
+__global__ void __launch_bounds__(kScanBlock) label_ids(int N, int* did, const int* __restrict__ boff,
+                                                       int* __restrict__ root, int max_drops) {
+  __shared__ int s_warp[kScanBlock / 32];
+  const int i = blockIdx.x * kScanBlock + threadIdx.x;
+  const int v = i < N ? did[i] : 0;
+  const int inc = block_inclusive_scan(v, s_warp);
+  if (i < N) {
+    const int id = boff[blockIdx.x] + inc - v;
+    did[i] = id;
+    if (v && id < max_drops) root[id] = i;
+  }
 }
 
 // ---------------------------------------------------------------- centres (D4)
 
-__device__ __forceinline__ long long min_image_i(long long d, int n) {
+__device__ __forceinline__ int min_image_i(int d, int n) {
   if (2 * d > n) d -= n;
   if (2 * d <= -n) d += n;
   return d;
 }
 
-// Sums of a lane group (lanes with equal key within the warp): every lane of the group gets the total.
-__device__ __forceinline__ long long group_sum(unsigned group, long long v) {
-  long long total = 0;
-  unsigned m = group;
-  while (m) {  // at most 32 iterations: one per member
-    const int src = __ffs(m) - 1;
-    total += __shfl_sync(group, v, src);
-    m &= m - 1;
+// Spreads the ids from the roots to every node (did[n] = id of n's droplet, -1 for background) and
+// adds each node's offset from its droplet's smallest node (minimum image) and a count of one to the
+// droplet's sums.  Lanes of a warp mostly see the same droplet: per distinct droplet in the warp one
+// 32-bit warp reduction and one 64-bit atomic per sum, so the sums are exact and order independent.
+__global__ void centre_sums(Geo g, const int* __restrict__ lab, int* did, const int* __restrict__ root,
+                            const Header* __restrict__ h, unsigned long long* cnt, long long* sx, long long* sy) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = g.nx * g.ny;
+  int d = -1;
+  if (n < N) {
+    const int l = lab[n];
+    d = l < 0 ? -1 : did[l];  // a root's entry holds its id; a root rewrites its own value unchanged
+    did[n] = d;
   }
-  return total;
-}
-
-__global__ void centre_sums(Geo g, const int* __restrict__ did, const int* __restrict__ root, int n_drops,
-                            unsigned long long* cnt, long long* sx, long long* sy) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool in = n < (long long)g.nx * g.ny;
-  const int d = in ? did[n] : -1;
+  const int n_drops = h->n_drops;
   const bool mine = d >= 0 && d < n_drops;
-  long long dx = 0, dy = 0;
+  int dx = 0, dy = 0;
   if (mine) {
     const int r = root[d];
-    const long long x = n % g.nx, y = n / g.nx, rx = r % g.nx, ry = r / g.nx;
+    const int x = n % g.nx, y = n / g.nx, rx = r % g.nx, ry = r / g.nx;
     dx = min_image_i(x - rx, g.nx);
     dy = g.periodic_y ? min_image_i(y - ry, g.ny) : (y - ry);
   }
-  // lanes of one warp mostly see the same droplet: one atomic per (warp, droplet) group, integer sums
   const unsigned active = __ballot_sync(0xffffffffu, mine);
   if (!mine) return;
-  const unsigned group = __match_any_sync(active, d);
-  const long long gx = group_sum(group, dx), gy = group_sum(group, dy);
-  const int lane = threadIdx.x & 31;
-  if (lane == __ffs(group) - 1) {
-    atomicAdd(cnt + d, (unsigned long long)__popc(group));
-    atomicAdd(reinterpret_cast<unsigned long long*>(sx + d), (unsigned long long)gx);
-    atomicAdd(reinterpret_cast<unsigned long long*>(sy + d), (unsigned long long)gy);
+  unsigned rest = active;
+  while (rest) {  // one iteration per distinct droplet among the active lanes (at most 32)
+    const int dl = __shfl_sync(active, d, __ffs(rest) - 1);
+    const bool in_group = d == dl;
+    const unsigned group = __ballot_sync(active, in_group);
+    const int gx = __reduce_add_sync(active, in_group ? dx : 0);
+    const int gy = __reduce_add_sync(active, in_group ? dy : 0);
+    if ((int)(threadIdx.x & 31) == __ffs(group) - 1) {
+      atomicAdd(cnt + dl, (unsigned long long)__popc(group));
+      atomicAdd(reinterpret_cast<unsigned long long*>(sx + dl), (unsigned long long)(long long)gx);
+      atomicAdd(reinterpret_cast<unsigned long long*>(sy + dl), (unsigned long long)(long long)gy);
+    }
+    rest &= ~group;
   }
 }
 
-__global__ void centre_final(Geo g, int n_drops, const int* __restrict__ root, const unsigned long long* __restrict__ cnt,
-                             const long long* __restrict__ sx, const long long* __restrict__ sy, double* cx, double* cy,
-                             int ncx, int ncy, int* __restrict__ ccount, int* __restrict__ dcell) {
-  const int d = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d >= n_drops) return;
-  const int r = root[d];
-  const double rx = (double)(r % g.nx), ry = (double)(r / g.nx);
-  double x = __dadd_rn(rx, __ddiv_rn((double)sx[d], (double)cnt[d]));
-  double y = __dadd_rn(ry, __ddiv_rn((double)sy[d], (double)cnt[d]));
-  if (x < 0.0) x = __dadd_rn(x, (double)g.nx);
-  else if (x >= (double)g.nx) x = __dsub_rn(x, (double)g.nx);
-  if (g.periodic_y) {
-    if (y < 0.0) y = __dadd_rn(y, (double)g.ny);
-    else if (y >= (double)g.ny) y = __dsub_rn(y, (double)g.ny);
+// Per droplet (grid-stride over the count in the header): the centre, wrapped into the lattice, and
+// its cell of the centre grid (kept in dcell) with the cell's count.
+__global__ void centre_final(Geo g, const Header* __restrict__ h, const int* __restrict__ root,
+                             const unsigned long long* __restrict__ cnt, const long long* __restrict__ sx,
+                             const long long* __restrict__ sy, double* cx, double* cy, int ncx, int ncy,
+                             int* __restrict__ ccount, int* __restrict__ dcell) {
+  const int n_drops = h->n_drops;
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n_drops; d += gridDim.x * blockDim.x) {
+    const int r = root[d];
+    const double rx = (double)(r % g.nx), ry = (double)(r / g.nx);
+    double x = __dadd_rn(rx, __ddiv_rn((double)sx[d], (double)cnt[d]));
+    double y = __dadd_rn(ry, __ddiv_rn((double)sy[d], (double)cnt[d]));
+    if (x < 0.0) x = __dadd_rn(x, (double)g.nx);
+    else if (x >= (double)g.nx) x = __dsub_rn(x, (double)g.nx);
+    if (g.periodic_y) {
+      if (y < 0.0) y = __dadd_rn(y, (double)g.ny);
+      else if (y >= (double)g.ny) y = __dsub_rn(y, (double)g.ny);
+    }
+    cx[d] = x;
+    cy[d] = y;
+    // cell of the centre: equal-width cells, nx / ncx by ny / ncy
+    int ix = (int)(x * ncx / g.nx), iy = (int)(y * ncy / g.ny);
+    ix = ix < 0 ? 0 : (ix >= ncx ? ncx - 1 : ix);
+    iy = iy < 0 ? 0 : (iy >= ncy ? ncy - 1 : iy);
+    const int c = iy * ncx + ix;
+    dcell[d] = c;
+    atomicAdd(ccount + c, 1);
   }
-  cx[d] = x;
-  cy[d] = y;
-  // cell of the centre: equal-width cells, nx / ncx by ny / ncy
-  int ix = (int)(x * ncx / g.nx), iy = (int)(y * ncy / g.ny);
-  ix = ix < 0 ? 0 : (ix >= ncx ? ncx - 1 : ix);
-  iy = iy < 0 ? 0 : (iy >= ncy ? ncy - 1 : iy);
-  const int c = iy * ncx + ix;
-  dcell[d] = c;
-  atomicAdd(ccount + c, 1);
 }
 
-__global__ void cell_fill(int n_drops, const int* __restrict__ dcell, const int* __restrict__ cstart, int* cfill,
-                          int* __restrict__ citems) {
-  const int d = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d >= n_drops) return;
-  const int c = dcell[d];
-  citems[cstart[c] + atomicAdd(cfill + c, 1)] = d;
+// One block: cell starts (exclusive scan of the counts) and the cell lists of droplet ids.
+__global__ void __launch_bounds__(kScanBlock) cell_fill(const Header* __restrict__ h, int ncell,
+                                                       const int* __restrict__ ccount, int* __restrict__ cstart,
+                                                       const int* __restrict__ dcell, int* cfill,
+                                                       int* __restrict__ citems) {
+  __shared__ int s_warp[kScanBlock / 32];
+  block_scan_loop(ccount, cstart, ncell, s_warp);
+  __syncthreads();  // the starts written by the other threads of this block are visible after the barrier
+  const int n_drops = h->n_drops;
+  for (int d = threadIdx.x; d < n_drops; d += kScanBlock) {
+    const int c = dcell[d];
+    citems[cstart[c] + atomicAdd(cfill + c, 1)] = d;
+  }
 }
 
 // ---------------------------------------------------------------- nearest centre (D5)
@@ -403,6 +517,7 @@ struct Grid {
   const int *cstart, *ccount, *citems;
   int ncx, ncy;
   double cw_min;  // smaller cell edge
+  float cw2_f;    // cw_min^2 rounded down to FP32
 };
 
 // Nearest centre to (x, y): rings of cells around the point's cell until no unvisited cell can hold a
@@ -454,41 +569,50 @@ __device__ int nearest_centre(const Geo& g, const Grid& G, double x, double y, d
   return best_id;
 }
 
-__global__ void voronoi_colour(Geo g, Grid G, int n_drops, int* __restrict__ col) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= (long long)g.nx * g.ny) return;
-  const int x = (int)(n % g.nx), y = (int)(n / g.nx);
-  if (is_solid(g, x, y) || n_drops == 0) {
-    col[n] = -1;
-    return;
-  }
-  col[n] = nearest_centre(g, G, (double)x, (double)y, nullptr);
-}
-
 // Tiled colouring: a CTA of 32 x 8 nodes stages the centres of every cell within 2 cells of the cells
 // its nodes lie in (x periodic; y periodic or clipped) into shared memory, and each node takes the
-// nearest staged centre (same distance arithmetic and tie rule as nearest_centre).  Any centre not
-// staged lies at least 3 cells from the node's own cell, so farther than 2 (conservatively 1) cell
-// edges: a node whose best staged distance is below one cell edge has its exact answer; otherwise
-// (and when the staging list overflows) it runs the full ring search.
-constexpr int kVTX = 32, kVTY = 8, kVList = 1024;
+// nearest staged centre.  Any centre not staged lies at least 3 cells from the node's own cell, so
+// farther than 2 (conservatively 1) cell edges: a node whose best staged distance is below one cell
+// edge has its exact answer; otherwise (and when the staging list overflows) it runs the full ring
+// search.
+//
+// The distances are screened in FP32.  Each centre is staged as its integer part and a two-float split
+// of its fraction; the node's integer offset from the integer part is exact and takes the minimum
+// image in integers, so only the small remaining offset is rounded: each screened component is within
+// two FP32 roundings of the exact offset, and a screened squared distance within 5e-7 (relative) of
+// the FP64 one (the oracle's unfused dx*dx + dy*dy).  When every other staged
+// centre screens above 1.00001 x the best + 1e-3, the best is the strict FP64 minimum and is taken as
+// it is; otherwise (a node within that margin of a Voronoi edge) the centres inside the margin are
+// compared in FP64 with the oracle's arithmetic and tie rule.  FP64 runs at 1/64 of the FP32 rate on
+// this part, so the screen decides almost every node without it.
+constexpr int kVTX = 32, kVTY = 8, kVList = 512;
 
-__global__ void __launch_bounds__(kVTX * kVTY) voronoi_tiled(Geo g, Grid G, int n_drops, int* __restrict__ col) {
+__global__ void __launch_bounds__(kVTX * kVTY) voronoi_tiled(Geo g, Grid G, const Header* __restrict__ h,
+                                                             int* __restrict__ col) {
   __shared__ double s_x[kVList], s_y[kVList];
-  __shared__ float s_xh[kVList], s_xl[kVList], s_yh[kVList], s_yl[kVList];  // two-float split of each centre
+  __shared__ float4 s_f[kVList];  // fraction of x (hi, lo), fraction of y (hi, lo)
+  __shared__ int2 s_i[kVList];    // integer parts
   __shared__ int s_id[kVList];
   __shared__ int s_n;
+  __shared__ int s_range[4];
+  const int n_drops = h->n_drops;
   const int x0 = blockIdx.x * kVTX, y0 = blockIdx.y * kVTY;
   const int tid = threadIdx.y * kVTX + threadIdx.x;
-  // cell range of the tile's nodes, widened by 2 cells
-  const int x1 = min(x0 + kVTX - 1, g.nx - 1), y1 = min(y0 + kVTY - 1, g.ny - 1);
-  const int cx0 = (int)((double)x0 * G.ncx / g.nx) - 2, cx1 = (int)((double)x1 * G.ncx / g.nx) + 2;
-  const int cy0 = (int)((double)y0 * G.ncy / g.ny) - 2, cy1 = (int)((double)y1 * G.ncy / g.ny) + 2;
-  const int wx = cx1 - cx0 + 1, wy = cy1 - cy0 + 1;
-  if (tid == 0) s_n = 0;
+  if (tid == 0) {
+    // cell range of the tile's nodes, widened by 2 cells: floor(x * ncx / nx) in exact integer
+    // arithmetic (the same cell as the FP64 quotient, whose rounding cannot cross an integer)
+    const long long x1 = min(x0 + kVTX - 1, g.nx - 1), y1 = min(y0 + kVTY - 1, g.ny - 1);
+    s_range[0] = (int)((long long)x0 * G.ncx / g.nx) - 2;
+    s_range[1] = (int)(x1 * G.ncx / g.nx) + 2;
+    s_range[2] = (int)((long long)y0 * G.ncy / g.ny) - 2;
+    s_range[3] = (int)(y1 * G.ncy / g.ny) + 2;
+    s_n = 0;
+  }
   __syncthreads();
+  const int cx0 = s_range[0], cy0 = s_range[2];
+  const int wx = s_range[1] - cx0 + 1, wy = s_range[3] - cy0 + 1;
   bool overflow = false;
-  for (int c = tid; c < wx * wy; c += kVTX * kVTY) {
+  for (int c = tid; c < wx * wy && n_drops > 0; c += kVTX * kVTY) {
     const int jy = cy0 + c / wx, jx = cx0 + c % wx;
     int cyi = jy;
     if (g.periodic_y) cyi = ((jy % G.ncy) + G.ncy) % G.ncy;
@@ -505,69 +629,88 @@ __global__ void __launch_bounds__(kVTX * kVTY) voronoi_tiled(Geo g, Grid G, int 
     for (int k = 0; k < n; ++k) {
       const int d = G.citems[s + k];
       const double cxd = G.cx[d], cyd = G.cy[d];
-      const float xh = __double2float_rn(cxd), yh = __double2float_rn(cyd);
+      const double ix = floor(cxd), iy = floor(cyd);
+      const double fxd = cxd - ix, fyd = cyd - iy;  // exact: the centre and its floor are within one
+      const float xh = __double2float_rn(fxd), yh = __double2float_rn(fyd);
       s_id[at + k] = d;
       s_x[at + k] = cxd;
       s_y[at + k] = cyd;
-      s_xh[at + k] = xh;
-      s_xl[at + k] = __double2float_rn(cxd - (double)xh);
-      s_yh[at + k] = yh;
-      s_yl[at + k] = __double2float_rn(cyd - (double)yh);
+      s_i[at + k] = make_int2((int)ix, (int)iy);
+      s_f[at + k] = make_float4(xh, __double2float_rn(fxd - (double)xh), yh, __double2float_rn(fyd - (double)yh));
     }
   }
   const int any_overflow = __syncthreads_or(overflow ? 1 : 0);
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
   if (x >= g.nx || y >= g.ny) return;
-  const long long n = (long long)y * g.nx + x;
+  const int n = y * g.nx + x;
   if (is_solid(g, x, y) || n_drops == 0) {
     col[n] = -1;
     return;
   }
-  const double px = (double)x, py = (double)y;
   int best_id = -1;
-  double best = 0.0;
+  bool settled = false;
   if (!any_overflow) {
-    const double hx = 0.5 * g.nx, hy = 0.5 * g.ny;
     const int m = s_n;
-    // FP32 screen: node minus the two-float centre is within a few ulps of the exact offset, so
-    // squared distances carry a relative error below 1e-6; only centres within 1e-5 (relative) of the
-    // best screened distance can hold the exact minimum or a tie, and only those are evaluated in
-    // FP64 below with the oracle's arithmetic.
-    const float fx = (float)x, fy = (float)y, fhx = 0.5f * g.nx, fhy = 0.5f * g.ny;
+    const float fhx = 0.5f * g.nx, fhy = 0.5f * g.ny;
     auto screen = [&](int k) {
-      float dx = (fx - s_xh[k]) - s_xl[k];
-      if (dx > fhx) dx -= (float)g.nx;
-      else if (dx < -fhx) dx += (float)g.nx;
-      float dy = (fy - s_yh[k]) - s_yl[k];
+      const int2 ci = s_i[k];
+      const float4 f = s_f[k];
+      // minimum image decided on the offset less the fraction's high part (as the oracle decides it on
+      // its offset; a decision that differs within an ulp of +-n/2 changes |dx| by an ulp), then the
+      // offset recomputed from the wrapped integer
+      const int dxi = x - ci.x, dyi = y - ci.y;
+      float dx = (float)dxi - f.x;
+      if (dx > fhx) dx = (float)(dxi - g.nx) - f.x;
+      else if (dx < -fhx) dx = (float)(dxi + g.nx) - f.x;
+      dx -= f.y;
+      float dy = (float)dyi - f.z;
       if (g.periodic_y) {
-        if (dy > fhy) dy -= (float)g.ny;
-        else if (dy < -fhy) dy += (float)g.ny;
+        if (dy > fhy) dy = (float)(dyi - g.ny) - f.z;
+        else if (dy < -fhy) dy = (float)(dyi + g.ny) - f.z;
       }
+      dy -= f.w;
       return dx * dx + dy * dy;
     };
-    float bf = 3.0e38f;
-    for (int k = 0; k < m; ++k) bf = fminf(bf, screen(k));
-    const float keep = bf * 1.00001f + 1e-3f;
+    float b1 = 3.0e38f, b2 = 3.0e38f;  // best and second-best screened distances
+    int k1 = -1;
     for (int k = 0; k < m; ++k) {
-      if (screen(k) > keep) continue;
-      double dx = __dsub_rn(px, s_x[k]);
-      if (dx > hx) dx = __dsub_rn(dx, (double)g.nx);
-      else if (dx < -hx) dx = __dadd_rn(dx, (double)g.nx);
-      double dy = __dsub_rn(py, s_y[k]);
-      if (g.periodic_y) {
-        if (dy > hy) dy = __dsub_rn(dy, (double)g.ny);
-        else if (dy < -hy) dy = __dadd_rn(dy, (double)g.ny);
-      }
-      const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-      const int d = s_id[k];
-      if (best_id < 0 || d2 < best || (d2 == best && d < best_id)) {
-        best = d2;
-        best_id = d;
+      const float d2 = screen(k);
+      if (d2 < b1) {
+        b2 = b1;
+        b1 = d2;
+        k1 = k;
+      } else if (d2 < b2) {
+        b2 = d2;
       }
     }
+    const float keep = b1 * 1.00001f + 1e-3f;
+    if (k1 >= 0 && b2 > keep) {
+      best_id = s_id[k1];
+      settled = keep < G.cw2_f;
+    } else if (k1 >= 0) {
+      const double px = (double)x, py = (double)y, hx = 0.5 * g.nx, hy = 0.5 * g.ny;
+      double best = 0.0;
+      for (int k = 0; k < m; ++k) {
+        if (screen(k) > keep) continue;
+        double dx = __dsub_rn(px, s_x[k]);
+        if (dx > hx) dx = __dsub_rn(dx, (double)g.nx);
+        else if (dx < -hx) dx = __dadd_rn(dx, (double)g.nx);
+        double dy = __dsub_rn(py, s_y[k]);
+        if (g.periodic_y) {
+          if (dy > hy) dy = __dsub_rn(dy, (double)g.ny);
+          else if (dy < -hy) dy = __dadd_rn(dy, (double)g.ny);
+        }
+        const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+        const int d = s_id[k];
+        if (best_id < 0 || d2 < best || (d2 == best && d < best_id)) {
+          best = d2;
+          best_id = d;
+        }
+      }
+      settled = best_id >= 0 && best < G.cw_min * G.cw_min;
+    }
   }
-  if (any_overflow || best_id < 0 || !(best < G.cw_min * G.cw_min))
-    best_id = nearest_centre(g, G, px, py, nullptr);
+  if (!settled) best_id = nearest_centre(g, G, (double)x, (double)y, nullptr);
   col[n] = best_id;
 }
 
@@ -587,14 +730,13 @@ __device__ __forceinline__ void adj_insert(int* adj, int* deg, int a, int b, int
 }
 
 __global__ void voronoi_links(Geo g, const int* __restrict__ col, int* adj, int* deg, int* err) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= (long long)g.nx * g.ny) return;
-  const int x = (int)(n % g.nx), y = (int)(n / g.nx);
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.nx * g.ny) return;
+  const int x = n % g.nx, y = n / g.nx;
   if (!g.periodic_y && y == g.ny - 1) return;
   const int x1 = x + 1 == g.nx ? 0 : x + 1, y1 = y + 1 == g.ny ? 0 : y + 1;
   // corners in cyclic order: 00, 10, 11, 01
-  const int c[4] = {col[(long long)y * g.nx + x], col[(long long)y * g.nx + x1], col[(long long)y1 * g.nx + x1],
-                    col[(long long)y1 * g.nx + x]};
+  const int c[4] = {col[y * g.nx + x], col[y * g.nx + x1], col[y1 * g.nx + x1], col[y1 * g.nx + x]};
   if (c[0] < 0 || c[1] < 0 || c[2] < 0 || c[3] < 0) return;
   int dist[4], k = 0;
 #pragma unroll
@@ -618,50 +760,83 @@ __global__ void voronoi_links(Geo g, const int* __restrict__ col, int* adj, int*
   }
 }
 
-// Sort each adjacency set (ascending; empty slots last) and count its links to larger ids.
-__global__ void adj_sort(int n_drops, int* adj, const int* __restrict__ deg, int* __restrict__ lcount) {
-  const int d = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d >= n_drops) return;
-  int* a = adj + (long long)d * kMaxDeg;
-  const int m = deg[d] < kMaxDeg ? deg[d] : kMaxDeg;
-  for (int i = 1; i < m; ++i) {
-    const int v = a[i];
-    int j = i - 1;
-    while (j >= 0 && a[j] > v) {
-      a[j + 1] = a[j];
-      --j;
+// One warp per droplet (grid-stride over the count in the header): sorts the adjacency set
+// ascending in registers (bitonic network over the 32 slots, empty slots last) and counts the links
+// to larger ids.  The filled slots of a set are a prefix (an insert takes the first empty slot).
+__global__ void adj_sort(const Header* __restrict__ h, int* adj, const int* __restrict__ deg,
+                         int* __restrict__ lcount) {
+  static_assert(kMaxDeg == 32, "one adjacency slot per lane");
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  const int n_drops = h->n_drops;
+  for (int d = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); d < n_drops; d += warps) {
+    int* a = adj + (size_t)d * kMaxDeg;
+    const int m = deg[d] < kMaxDeg ? deg[d] : kMaxDeg;
+    int v = lane < m ? a[lane] : 0x7fffffff;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const int o = __shfl_xor_sync(0xffffffffu, v, j);
+        const bool up = (lane & k) == 0, low = (lane & j) == 0;
+        v = (low == up) ? min(v, o) : max(v, o);
+      }
     }
-    a[j + 1] = v;
+    if (lane < m) a[lane] = v;
+    const unsigned larger = __ballot_sync(0xffffffffu, lane < m && v > d);
+    if (lane == 0) lcount[d] = __popc(larger);
   }
-  int c = 0;
-  for (int i = 0; i < m; ++i) c += a[i] > d ? 1 : 0;
-  lcount[d] = c;
 }
 
-__global__ void links_write(int n_drops, const int* __restrict__ adj, const int* __restrict__ deg,
-                            const int* __restrict__ loff, int* __restrict__ links) {
-  const int d = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d >= n_drops) return;
-  const int* a = adj + (long long)d * kMaxDeg;
-  const int m = deg[d] < kMaxDeg ? deg[d] : kMaxDeg;
-  int o = loff[d];
-  for (int i = 0; i < m; ++i)
-    if (a[i] > d) {
-      links[2 * o] = d;
-      links[2 * o + 1] = a[i];
-      ++o;
-    }
+// One block: link offsets (exclusive scan of the per-droplet counts) and the link count in the header.
+__global__ void __launch_bounds__(kScanBlock) links_count(Header* h, const int* __restrict__ lcount,
+                                                         int* __restrict__ loff) {
+  __shared__ int s_warp[kScanBlock / 32];
+  const int total = block_scan_loop(lcount, loff, h->n_drops, s_warp);
+  if (threadIdx.x == 0) h->n_links = total;
 }
 
-__global__ void write_header(Header* h, const int* __restrict__ dscan_total, const int* __restrict__ lscan_total,
-                             int max_drops, int stage) {
-  if (stage == 0) {
-    const int m = *dscan_total;
-    h->n_drops = m < max_drops ? m : max_drops;
-    if (m > max_drops) h->err |= kErrDrops;
-  } else {
-    h->n_links = *lscan_total;
+// Per droplet d (grid-stride): its links (d, b) with b > d, ascending, at its offset (at most
+// max_links in all; only an adjacency overflow, reported as kErrDegree, can reach that bound).
+__global__ void links_write(const Header* __restrict__ h, const int* __restrict__ adj, const int* __restrict__ deg,
+                            const int* __restrict__ loff, int* __restrict__ links, long long max_links) {
+  const int n_drops = h->n_drops;
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n_drops; d += gridDim.x * blockDim.x) {
+    const int* a = adj + (size_t)d * kMaxDeg;
+    const int m = deg[d] < kMaxDeg ? deg[d] : kMaxDeg;
+    int o = loff[d];
+    for (int i = 0; i < m; ++i) {
+      const int b = a[i];
+      if (b > d && o < max_links) {
+        links[2 * o] = d;
+        links[2 * o + 1] = b;
+        ++o;
+      }
+    }
   }
+}
+
+// Resets one analysis: the header (sizes, zero counts and error bits) and every per-droplet and
+// per-cell accumulator the pipeline adds into (grid-stride over the largest of them).
+__global__ void drop_reset(Header* h, Header init, unsigned long long* cnt, long long* sx, long long* sy, int* adj,
+                           int* deg, int* ccount, int* cfill, int ncell) {
+  const int M = init.max_drops;
+  const long long total = (long long)M * kMaxDeg > ncell ? (long long)M * kMaxDeg : ncell;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (i < (long long)M * kMaxDeg) adj[i] = -1;
+    if (i < M) {
+      cnt[i] = 0;
+      sx[i] = 0;
+      sy[i] = 0;
+      deg[i] = 0;
+    }
+    if (i < ncell) {
+      ccount[i] = 0;
+      cfill[i] = 0;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *h = init;
 }
 
 // ---------------------------------------------------------------- T1 comparison
@@ -827,6 +1002,8 @@ Grid grid_of(const DView& v, const DLayout& L, const lb_params& p) {
   G.ncy = L.ncy;
   const double wx = (double)p.nx / L.ncx, wy = (double)p.ny / L.ncy;
   G.cw_min = wx < wy ? wx : wy;
+  G.cw2_f = (float)(G.cw_min * G.cw_min);
+  if ((double)G.cw2_f > G.cw_min * G.cw_min) G.cw2_f = std::nextafter(G.cw2_f, 0.0f);
   return G;
 }
 
@@ -864,7 +1041,6 @@ int lb_droplets(lb_handle* h, double threshold, int max_drops, void* d_ws, size_
   const DView v = view(d_ws, L);
   const Geo g{h->p.nx, h->p.ny, h->p.periodic_y, h->cfg.mask};
   cudaStream_t s = h->stream;
-  const long long N = L.N;
   double* stage = static_cast<double*>(h->buf[h->cur ^ 1]);  // rho1 is plane 0 of the fields
   Header hdr{};
   hdr.max_drops = max_drops;
@@ -873,61 +1049,42 @@ int lb_droplets(lb_handle* h, double threshold, int max_drops, void* d_ws, size_
   hdr.periodic_y = h->p.periodic_y;
   hdr.ncx = L.ncx;
   hdr.ncy = L.ncy;
-  cudaError_t e = fields_into(h, stage);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(v.hdr, &hdr, sizeof hdr, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(v.cnt, 0, (size_t)max_drops * 8, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(v.sx, 0, (size_t)max_drops * 8, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(v.sy, 0, (size_t)max_drops * 8, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(v.adj, 0xff, (size_t)max_drops * kMaxDeg * 4, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(v.deg, 0, (size_t)max_drops * 4, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(v.ccount, 0, (size_t)L.ncell * 4, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(v.cfill, 0, (size_t)L.ncell * 4, s);
-  if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets", e);
+  const int N = (int)L.N;  // nx * ny fits in 31 bits (lb_init)
   const int T = 256;
+  // per-droplet kernels run grid-stride over the count the labelling wrote into the header
+  auto capped = [](unsigned blocks) { return blocks < kGridCap ? blocks : kGridCap; };
+  const unsigned per_drop = capped(nb(max_drops, T)), per_drop_warps = capped(nb((long long)max_drops * 32, T));
+  const unsigned reset_blocks =
+      capped(nb((long long)max_drops * kMaxDeg > L.ncell ? (long long)max_drops * kMaxDeg : L.ncell, T));
   int* err = &v.hdr->err;
-  label_init<<<nb(N, T), T, 0, s>>>(stage, threshold, g, v.lab);
-  label_merge<<<nb(N, T), T, 0, s>>>(g, v.lab, err);
-  label_flatten<<<nb(N, T), T, 0, s>>>(N, v.lab, v.did);
-  e = exclusive_scan(v.did, N, v.did, v.blk, s);  // ids of the roots, in node order
-  if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets scan", e);
-  write_header<<<1, 1, 0, s>>>(v.hdr, v.blk + L.nblk, nullptr, max_drops, 0);
-  label_ids<<<nb(N, T), T, 0, s>>>(N, v.lab, v.did, v.root, max_drops, err);
-  label_ids_spread<<<nb(N, T), T, 0, s>>>(N, v.lab, v.did);
-  e = cudaGetLastError();
-  Header got{};
-  if (e == cudaSuccess) {
-    if (int rc = read_header(h, v.hdr, &got)) return rc;
-  } else {
-    return dfail(h, LB_ECUDA, "lb_droplets labels", e);
-  }
-  if (got.err & kErrUnion) return dfail(h, LB_ECUDA, "droplet labelling did not converge");
-  if (got.err & kErrDrops) return dfail(h, LB_ENOSPACE, "more droplets than max_drops");
-  const int M = got.n_drops;
-  if (M > 0) {
-    centre_sums<<<nb(N, T), T, 0, s>>>(g, v.did, v.root, M, v.cnt, v.sx, v.sy);
-    // cell of each droplet kept in lcount until the links need it
-    centre_final<<<nb(M, T), T, 0, s>>>(g, M, v.root, v.cnt, v.sx, v.sy, v.cx, v.cy, L.ncx, L.ncy, v.ccount, v.lcount);
-    e = exclusive_scan(v.ccount, L.ncell, v.cstart, v.cblk, s);
-    if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets cells", e);
-    cell_fill<<<nb(M, T), T, 0, s>>>(M, v.lcount, v.cstart, v.cfill, v.citems);
-  }
+  cudaError_t e = fields_into(h, stage);
+  if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets fields", e);
+  drop_reset<<<reset_blocks, T, 0, s>>>(v.hdr, hdr, v.cnt, v.sx, v.sy, v.adj, v.deg, v.ccount, v.cfill, L.ncell);
+  // labels (D1-D3): tile-local union-find, unions across tile borders, roots and their ids
+  const int ncol = (h->p.nx + kLT - 1) / kLT, nrow = (h->p.ny + kLT - 1) / kLT;
+  label_local<<<dim3((unsigned)ncol, (unsigned)nrow), kLThreads, 0, s>>>(stage, threshold, g, v.lab, err);
+  label_border<<<nb((long long)h->p.ny * ncol + (long long)h->p.nx * nrow, T), T, 0, s>>>(g, ncol, nrow, v.lab, err);
+  label_flatten<<<L.nblk, kScanBlock, 0, s>>>(N, v.lab, v.did, v.blk, err);
+  label_count<<<1, kScanBlock, 0, s>>>(v.blk, L.nblk, v.hdr, max_drops);
+  label_ids<<<L.nblk, kScanBlock, 0, s>>>(N, v.did, v.blk, v.root, max_drops);
+  // centres (D4) and the cell grid of the centres
+  centre_sums<<<nb(N, T), T, 0, s>>>(g, v.lab, v.did, v.root, v.hdr, v.cnt, v.sx, v.sy);
+  centre_final<<<per_drop, T, 0, s>>>(g, v.hdr, v.root, v.cnt, v.sx, v.sy, v.cx, v.cy, L.ncx, L.ncy, v.ccount, v.lcount);
+  cell_fill<<<1, kScanBlock, 0, s>>>(v.hdr, L.ncell, v.ccount, v.cstart, v.lcount, v.cfill, v.citems);
+  // colours (D5) and links (D6)
   const Grid G = grid_of(v, L, h->p);
   voronoi_tiled<<<dim3((unsigned)((h->p.nx + kVTX - 1) / kVTX), (unsigned)((h->p.ny + kVTY - 1) / kVTY)),
-                  dim3(kVTX, kVTY), 0, s>>>(g, G, M, v.col);
-  if (M > 0) {
-    voronoi_links<<<nb(N, T), T, 0, s>>>(g, v.col, v.adj, v.deg, err);
-    adj_sort<<<nb(M, T), T, 0, s>>>(M, v.adj, v.deg, v.lcount);
-    e = exclusive_scan(v.lcount, M, v.loff, v.dblk, s);
-    if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets links", e);
-    links_write<<<nb(M, T), T, 0, s>>>(M, v.adj, v.deg, v.loff, v.links);
-    write_header<<<1, 1, 0, s>>>(v.hdr, nullptr, v.dblk + nb(M, kScanBlock), max_drops, 1);
-  } else {
-    e = cudaMemsetAsync(&v.hdr->n_links, 0, sizeof(int), s);
-    if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets", e);
-  }
+                  dim3(kVTX, kVTY), 0, s>>>(g, G, v.hdr, v.col);
+  voronoi_links<<<nb(N, T), T, 0, s>>>(g, v.col, v.adj, v.deg, err);
+  adj_sort<<<per_drop_warps, T, 0, s>>>(v.hdr, v.adj, v.deg, v.lcount);
+  links_count<<<1, kScanBlock, 0, s>>>(v.hdr, v.lcount, v.loff);
+  links_write<<<per_drop, T, 0, s>>>(v.hdr, v.adj, v.deg, v.loff, v.links, L.max_links);
   e = cudaGetLastError();
   if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets", e);
+  Header got{};
   if (int rc = read_header(h, v.hdr, &got)) return rc;
+  if (got.err & kErrUnion) return dfail(h, LB_ECUDA, "droplet labelling did not converge");
+  if (got.err & kErrDrops) return dfail(h, LB_ENOSPACE, "more droplets than max_drops");
   if (got.err & kErrDegree) return dfail(h, LB_ENOSPACE, "a droplet has more Voronoi neighbours than the adjacency holds");
   if (n_drops) *n_drops = got.n_drops;
   if (n_links) *n_links = got.n_links;

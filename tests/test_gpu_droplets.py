@@ -82,6 +82,24 @@ def test_ragged_periodic_and_posts(nx, ny, periodic, posts):
     _compare(g, g.droplets(BTH), params, mask=mask)
 
 
+@pytest.mark.parametrize("nx,ny,periodic,p", [(100, 70, 1, 0.45), (161, 67, 0, 0.62), (33, 200, 1, 0.58)])
+def test_percolation_clusters_across_tiles(nx, ny, periodic, p):
+    """Site-percolation fields: hundreds of clusters of every shape, near the threshold one that spans
+    the lattice through many 32 x 32 labelling tiles and the periodic seams, and centres on the
+    integer and half-integer grid, so that many nodes are exactly equidistant from two centres (the
+    tie rule); labels, centres, colours and links against the oracle."""
+    rng = np.random.default_rng(7 + nx)
+    r1 = np.where(rng.random((ny, nx)) < p, 1.4, 0.1)
+    params = dict(I.EMULSION_PARAMS, nx=nx, ny=ny, periodic_y=periodic, alpha_g=0.0, T_down=0.0, T_up=0.0)
+    g = lb.Lattice(params, r1, 1.5 - r1, 0.0)
+    d = g.droplets(BTH, max_drops=nx * ny)
+    o = _compare(g, d, params)
+    assert o["n"] > 50
+    if p > 0.6:  # above the site-percolation threshold: the largest cluster crosses the tile grid
+        ys, xs = np.nonzero(d["label"] == np.argmax(d["size"]))
+        assert np.ptp(xs) > 64 and np.ptp(ys) > 32
+
+
 def test_degenerate_cases():
     w = I.emulsion_small(nx=48, ny=32, n_drops=1, R=5.0)
     g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0)
