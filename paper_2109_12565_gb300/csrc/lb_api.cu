@@ -433,6 +433,8 @@ void lb_destroy(lb_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
   }
   drop_graphs(h);
+  for (auto& d : h->dgraph)
+    if (d.exec) cudaGraphExecDestroy(d.exec);
   if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
 }

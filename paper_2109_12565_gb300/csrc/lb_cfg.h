@@ -9,7 +9,7 @@ namespace tlb {
 
 // MODE_STEP_NU: a step that also sums u^(H)_y T over the fluid nodes of its input state, one partial
 // per warp (the Nusselt number's advective part, Eq. NuTime), for the adjoint's forward pass.
-enum Mode : int { MODE_STEP = 0, MODE_OBS = 1, MODE_FIELDS = 2, MODE_STEP_NU = 3 };
+enum Mode : int { MODE_STEP = 0, MODE_OBS = 1, MODE_FIELDS = 2, MODE_STEP_NU = 3, MODE_RHO1 = 4 };
 __host__ __device__ constexpr bool mode_needs_T(int m) { return m == MODE_OBS || m == MODE_FIELDS; }
 __host__ __device__ constexpr bool mode_steps(int m) { return m == MODE_STEP || m == MODE_STEP_NU; }
 
@@ -51,7 +51,8 @@ inline dim3 grid_for(int nx, int ny, int tx, int ty) {
 
 // ---- launchers (one translation unit per storage precision) ----
 // mode MODE_STEP: fin -> fout;  MODE_OBS: aux = per-block partials (kObsSlots doubles each);
-// MODE_FIELDS: aux = 5 planes of nx*ny doubles (rho1, rho2, T, ux, uy).
+// MODE_FIELDS: aux = 5 planes of nx*ny doubles (rho1, rho2, T, ux, uy); MODE_RHO1: aux = the rho1
+// plane alone, the same values (fout unused).
 cudaError_t launch_f64(int mode, const StepCfg& c, const void* fin, void* fout, double* aux, cudaStream_t s);
 cudaError_t launch_f32(int mode, const StepCfg& c, const void* fin, void* fout, double* aux, cudaStream_t s);
 cudaError_t launch_f32h(int mode, const StepCfg& c, const void* fin, void* fout, double* aux, cudaStream_t s);

@@ -14,14 +14,16 @@
 //       pairs of neighbouring corners.
 //
 // Pipeline (all on the caller's stream, no host round trip until the counts are read; the
-// per-droplet kernels take the droplet count from the workspace header the labelling wrote):
-//   fields (MODE_FIELDS of the step kernel) -> reset of the accumulators -> labels: union-find with
-//   atomicMin hooks, so every root ends as its component's smallest node, first inside 32 x 32 tiles
-//   in shared memory, then across the tile borders -> ids: block scan of the root flags -> centres:
-//   64-bit integer sums of the unwrapped offsets (exact, order independent) -> cell grid of the
-//   centres -> colours: nearest staged centre, screened in FP32 and settled in FP64 near Voronoi
-//   edges -> links: a bounded adjacency set per droplet (atomicCAS), sorted per droplet in a warp,
-//   compacted by a scan.  Every result is independent of thread scheduling.
+// per-droplet kernels take the droplet count from the workspace header the labelling wrote; the
+// launch sequence is captured once per workspace, bound, threshold and buffer into a CUDA graph):
+//   rho_1 (MODE_RHO1: the field mode's rho_1, from the 9 planes of component 1) -> reset of the
+//   accumulators -> labels: union-find with atomicMin hooks, so every root ends as its component's
+//   smallest node, first inside 32 x 32 tiles in shared memory, then across the tile borders -> ids:
+//   root bits per 32 nodes and a scan of their counts -> centres: 64-bit integer sums of the
+//   unwrapped offsets (exact, order independent) -> cell grid of the centres -> colours: nearest
+//   staged centre, screened in FP32 and settled in FP64 near Voronoi edges -> links: a bounded
+//   adjacency set per droplet (atomicCAS), sorted per droplet in a warp, compacted by a scan.
+//   Every result is independent of thread scheduling.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -49,8 +51,17 @@ struct Header {
   int pad[7];
 };
 
+// A centre as the colouring stages it: the FP64 centre (the oracle's values), its integer parts and
+// a two-float split of its fractions.  Written per droplet by centre_final, sorted by cell in cell_fill.
+struct alignas(16) CRec {
+  double x, y;
+  float4 f;  // fraction of x (hi, lo), fraction of y (hi, lo)
+  int2 i;    // floor(x), floor(y)
+  int id, pad;
+};
+
 struct DLayout {
-  size_t hdr, lab, did, col, blk, cnt, sx, sy, root, cx, cy, adj, deg, lcount, loff, dblk, ccount, cstart, cfill,
+  size_t hdr, lab, did, col, rmask, woff, crec_id, crec, blk, cnt, sx, sy, root, cx, cy, adj, deg, lcount, loff, dblk, ccount, cstart, cfill,
       citems, cblk, links, total;
   long long N;
   int nblk, max_drops, ncx, ncy, ncell, dnblk, cnblk;
@@ -79,6 +90,8 @@ inline DLayout layout(int nx, int ny, int max_drops) {
   L.lab = take((size_t)L.N * 4);
   L.did = take((size_t)L.N * 4);
   L.col = take((size_t)L.N * 4);
+  L.rmask = take((size_t)(L.N + 31) / 32 * 4);
+  L.woff = take((size_t)(L.N + 31) / 32 * 4);
   L.blk = take((size_t)(L.nblk + 1) * 4);
   L.cnt = take(M * 8);
   L.sx = take(M * 8);
@@ -95,6 +108,8 @@ inline DLayout layout(int nx, int ny, int max_drops) {
   L.cstart = take((size_t)L.ncell * 4);
   L.cfill = take((size_t)L.ncell * 4);
   L.citems = take(M * 4);
+  L.crec_id = take(M * sizeof(CRec));
+  L.crec = take(M * sizeof(CRec));
   L.cblk = take((size_t)(L.cnblk + 1) * 4);
   L.links = take((size_t)L.max_links * 2 * 4);
   L.total = off;
@@ -105,11 +120,14 @@ inline DLayout layout(int nx, int ny, int max_drops) {
 struct DView {
   Header* hdr;
   int *lab, *did, *col, *blk;
+  unsigned* rmask;  // per 32 nodes: the bits of the roots
+  int* woff;        // per 32 nodes: the number of roots before them
   unsigned long long* cnt;
   long long *sx, *sy;
   int* root;
   double *cx, *cy;
   int *adj, *deg, *lcount, *loff, *dblk, *ccount, *cstart, *cfill, *citems, *cblk, *links;
+  CRec *crec_id, *crec;  // centre records by droplet id, and sorted by cell
 };
 
 inline DView view(void* ws, const DLayout& L) {
@@ -119,6 +137,8 @@ inline DView view(void* ws, const DLayout& L) {
   v.lab = reinterpret_cast<int*>(b + L.lab);
   v.did = reinterpret_cast<int*>(b + L.did);
   v.col = reinterpret_cast<int*>(b + L.col);
+  v.rmask = reinterpret_cast<unsigned*>(b + L.rmask);
+  v.woff = reinterpret_cast<int*>(b + L.woff);
   v.blk = reinterpret_cast<int*>(b + L.blk);
   v.cnt = reinterpret_cast<unsigned long long*>(b + L.cnt);
   v.sx = reinterpret_cast<long long*>(b + L.sx);
@@ -135,6 +155,8 @@ inline DView view(void* ws, const DLayout& L) {
   v.cstart = reinterpret_cast<int*>(b + L.cstart);
   v.cfill = reinterpret_cast<int*>(b + L.cfill);
   v.citems = reinterpret_cast<int*>(b + L.citems);
+  v.crec_id = reinterpret_cast<CRec*>(b + L.crec_id);
+  v.crec = reinterpret_cast<CRec*>(b + L.crec);
   v.cblk = reinterpret_cast<int*>(b + L.cblk);
   v.links = reinterpret_cast<int*>(b + L.links);
   return v;
@@ -342,29 +364,30 @@ __global__ void label_border(Geo g, int ncol, int nrow, int* lab, int* err) {
   if (!unite(lab, n, m, 1 << 26)) atomicOr(err, kErrUnion);
 }
 
-// Final labels (the roots), the root flags in flag, and per 1024-node block the number of roots
-// (the first pass of the id scan).
-__global__ void __launch_bounds__(kScanBlock) label_flatten(int N, int* lab, int* __restrict__ flag,
+// Final labels (the roots), the root bits of every 32 nodes (rmask) and per 1024-node block the number
+// of roots (the first pass of the id scan).
+__global__ void __launch_bounds__(kScanBlock) label_flatten(int N, int* lab, unsigned* __restrict__ rmask,
                                                            int* __restrict__ bsum, int* err) {
   __shared__ int s_warp[kScanBlock / 32];
   const int n = blockIdx.x * kScanBlock + threadIdx.x;
-  int f = 0;
+  bool root = false;
   if (n < N) {
     const int l = lab[n];
     if (l >= 0) {
       const int r = find_root(lab, n, 1 << 26);
       if (r >= 0) {
         lab[n] = r;  // every node of a chain resolves to the same root; concurrent writes store roots only
-        f = r == n ? 1 : 0;
+        root = r == n;
       } else {
         atomicOr(err, kErrUnion);
       }
     }
-    flag[n] = f;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
-  if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = f;
+  const unsigned bits = __ballot_sync(0xffffffffu, root);
+  if ((threadIdx.x & 31) == 0) {
+    if (n < N) rmask[n >> 5] = bits;
+    s_warp[threadIdx.x >> 5] = __popc(bits);
+  }
   __syncthreads();
   if (threadIdx.x < 32) {
     int w = s_warp[threadIdx.x];
@@ -401,19 +424,24 @@ __global__ void __launch_bounds__(kScanBlock) label_count(int* bsum, int nb, Hea
   }
 }
 
-// Second pass of the id scan: did[n] = number of roots before n (ids in root order, D3) and the root
-// table root[id] = node.
-__global__ void __launch_bounds__(kScanBlock) label_ids(int N, int* did, const int* __restrict__ boff,
-                                                       int* __restrict__ root, int max_drops) {
-  __shared__ int s_warp[kScanBlock / 32];
-  const int i = blockIdx.x * kScanBlock + threadIdx.x;
-  const int v = i < N ? did[i] : 0;
-  const int inc = block_inclusive_scan(v, s_warp);
-  if (i < N) {
-    const int id = boff[blockIdx.x] + inc - v;
-    did[i] = id;
-    if (v && id < max_drops) root[id] = i;
+// Second pass of the id scan, per 32 nodes: woff[w] = number of roots before node 32 w (the block's
+// offset plus a warp scan of the root counts of the block's 32 words).  A root's id (D3) is then
+// woff[n / 32] plus the number of roots below it in its word.
+__global__ void warp_offsets(int n_words, const unsigned* __restrict__ rmask, const int* __restrict__ boff,
+                             int* __restrict__ woff) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;  // blockDim is a multiple of 32: a warp = one scan block
+  const int c = w < n_words ? __popc(rmask[w]) : 0;
+  int inc = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if ((threadIdx.x & 31) >= o) inc += t;
   }
+  if (w < n_words) woff[w] = boff[w >> 5] + inc - c;
+}
+
+__device__ __forceinline__ int root_id(const unsigned* __restrict__ rmask, const int* __restrict__ woff, int r) {
+  return woff[r >> 5] + __popc(rmask[r >> 5] & ((1u << (r & 31)) - 1u));
 }
 
 // ---------------------------------------------------------------- centres (D4)
@@ -424,26 +452,28 @@ __device__ __forceinline__ int min_image_i(int d, int n) {
   return d;
 }
 
-// Spreads the ids from the roots to every node (did[n] = id of n's droplet, -1 for background) and
-// adds each node's offset from its droplet's smallest node (minimum image) and a count of one to the
-// droplet's sums.  Lanes of a warp mostly see the same droplet: per distinct droplet in the warp one
-// 32-bit warp reduction and one 64-bit atomic per sum, so the sums are exact and order independent.
-__global__ void centre_sums(Geo g, const int* __restrict__ lab, int* did, const int* __restrict__ root,
-                            const Header* __restrict__ h, unsigned long long* cnt, long long* sx, long long* sy) {
+// Writes every node's droplet id (did, -1 for background) and the root table (root[id] = the
+// droplet's smallest node), and adds each node's offset from that node (minimum image) and a count
+// of one to the droplet's sums.  Lanes of a warp mostly see the same droplet: per distinct droplet
+// in the warp one 32-bit warp reduction and one 64-bit atomic per sum, so the sums are exact and
+// order independent.
+__global__ void centre_sums(Geo g, const int* __restrict__ lab, const unsigned* __restrict__ rmask,
+                            const int* __restrict__ woff, const Header* __restrict__ h, int* __restrict__ did,
+                            int* __restrict__ root, unsigned long long* cnt, long long* sx, long long* sy) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = g.nx * g.ny;
-  int d = -1;
+  int d = -1, l = -1;
   if (n < N) {
-    const int l = lab[n];
-    d = l < 0 ? -1 : did[l];  // a root's entry holds its id; a root rewrites its own value unchanged
+    l = lab[n];
+    if (l >= 0) d = root_id(rmask, woff, l);
     did[n] = d;
   }
   const int n_drops = h->n_drops;
   const bool mine = d >= 0 && d < n_drops;
+  if (mine && l == n) root[d] = n;
   int dx = 0, dy = 0;
   if (mine) {
-    const int r = root[d];
-    const int x = n % g.nx, y = n / g.nx, rx = r % g.nx, ry = r / g.nx;
+    const int x = n % g.nx, y = n / g.nx, rx = l % g.nx, ry = l / g.nx;
     dx = min_image_i(x - rx, g.nx);
     dy = g.periodic_y ? min_image_i(y - ry, g.ny) : (y - ry);
   }
@@ -470,7 +500,7 @@ __global__ void centre_sums(Geo g, const int* __restrict__ lab, int* did, const 
 __global__ void centre_final(Geo g, const Header* __restrict__ h, const int* __restrict__ root,
                              const unsigned long long* __restrict__ cnt, const long long* __restrict__ sx,
                              const long long* __restrict__ sy, double* cx, double* cy, int ncx, int ncy,
-                             int* __restrict__ ccount, int* __restrict__ dcell) {
+                             int* __restrict__ ccount, int* __restrict__ dcell, CRec* __restrict__ rec) {
   const int n_drops = h->n_drops;
   for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n_drops; d += gridDim.x * blockDim.x) {
     const int r = root[d];
@@ -485,6 +515,18 @@ __global__ void centre_final(Geo g, const Header* __restrict__ h, const int* __r
     }
     cx[d] = x;
     cy[d] = y;
+    CRec cr;
+    cr.x = x;
+    cr.y = y;
+    const double fx0 = floor(x), fy0 = floor(y);
+    const double fx = __dsub_rn(x, fx0), fy = __dsub_rn(y, fy0);  // exact: a number and its floor are within one
+    const float fxh = __double2float_rn(fx), fyh = __double2float_rn(fy);
+    cr.f = make_float4(fxh, __double2float_rn(__dsub_rn(fx, (double)fxh)), fyh,
+                       __double2float_rn(__dsub_rn(fy, (double)fyh)));
+    cr.i = make_int2((int)fx0, (int)fy0);
+    cr.id = d;
+    cr.pad = 0;
+    rec[d] = cr;
     // cell of the centre: equal-width cells, nx / ncx by ny / ncy
     int ix = (int)(x * ncx / g.nx), iy = (int)(y * ncy / g.ny);
     ix = ix < 0 ? 0 : (ix >= ncx ? ncx - 1 : ix);
@@ -495,18 +537,22 @@ __global__ void centre_final(Geo g, const Header* __restrict__ h, const int* __r
   }
 }
 
-// One block: cell starts (exclusive scan of the counts) and the cell lists of droplet ids.
+// One block: cell starts (exclusive scan of the counts), the cell lists of droplet ids and the centre
+// records in the same order.
 __global__ void __launch_bounds__(kScanBlock) cell_fill(const Header* __restrict__ h, int ncell,
                                                        const int* __restrict__ ccount, int* __restrict__ cstart,
                                                        const int* __restrict__ dcell, int* cfill,
-                                                       int* __restrict__ citems) {
+                                                       int* __restrict__ citems, const CRec* __restrict__ rec_id,
+                                                       CRec* __restrict__ rec) {
   __shared__ int s_warp[kScanBlock / 32];
   block_scan_loop(ccount, cstart, ncell, s_warp);
   __syncthreads();  // the starts written by the other threads of this block are visible after the barrier
   const int n_drops = h->n_drops;
   for (int d = threadIdx.x; d < n_drops; d += kScanBlock) {
     const int c = dcell[d];
-    citems[cstart[c] + atomicAdd(cfill + c, 1)] = d;
+    const int at = cstart[c] + atomicAdd(cfill + c, 1);
+    citems[at] = d;
+    rec[at] = rec_id[d];
   }
 }
 
@@ -569,50 +615,56 @@ __device__ int nearest_centre(const Geo& g, const Grid& G, double x, double y, d
   return best_id;
 }
 
-// Tiled colouring: a CTA of 32 x 8 nodes stages the centres of every cell within 2 cells of the cells
-// its nodes lie in (x periodic; y periodic or clipped) into shared memory, and each node takes the
-// nearest staged centre.  Any centre not staged lies at least 3 cells from the node's own cell, so
-// farther than 2 (conservatively 1) cell edges: a node whose best staged distance is below one cell
-// edge has its exact answer; otherwise (and when the staging list overflows) it runs the full ring
-// search.
-//
-// The distances are screened in FP32.  Each centre is staged as its integer part and a two-float split
-// of its fraction; the node's integer offset from the integer part is exact and takes the minimum
-// image in integers, so only the small remaining offset is rounded: each screened component is within
-// two FP32 roundings of the exact offset, and a screened squared distance within 5e-7 (relative) of
-// the FP64 one (the oracle's unfused dx*dx + dy*dy).  When every other staged
-// centre screens above 1.00001 x the best + 1e-3, the best is the strict FP64 minimum and is taken as
-// it is; otherwise (a node within that margin of a Voronoi edge) the centres inside the margin are
-// compared in FP64 with the oracle's arithmetic and tie rule.  FP64 runs at 1/64 of the FP32 rate on
-// this part, so the screen decides almost every node without it.
-constexpr int kVTX = 32, kVTY = 8, kVList = 512;
+// ---------------------------------------------------------------- colours and links (D5, D6)
 
-__global__ void __launch_bounds__(kVTX * kVTY) voronoi_tiled(Geo g, Grid G, const Header* __restrict__ h,
-                                                             int* __restrict__ col) {
-  __shared__ double s_x[kVList], s_y[kVList];
-  __shared__ float4 s_f[kVList];  // fraction of x (hi, lo), fraction of y (hi, lo)
-  __shared__ int2 s_i[kVList];    // integer parts
-  __shared__ int s_id[kVList];
-  __shared__ int s_n;
-  __shared__ int s_range[4];
+// Colours of one 32 x 8 tile per CTA (one node per thread).
+//
+// Staging: the records of every cell within 2 cells of the cells the tile's nodes lie in (x periodic;
+// y periodic or clipped) go to shared memory.  Any centre not staged lies at least 2 cells from a
+// node's cell, so farther than 1 cell edge (a conservative bound): a node whose best staged distance
+// is below one cell edge has its exact answer; otherwise (and when the staging list overflows) it runs
+// the full ring search.  The staged list is then cut to the centres that can be nearest to a node of
+// the tile: the centre nearest to the tile's middle bounds every node's nearest distance by U (its
+// distance + the half-diagonal), and a centre farther than U from the tile box is nobody's nearest
+// (nor tied).  FP32 with margins far above its rounding (1e-4 relative, 1e-2 absolute) keeps U an
+// upper bound.
+//
+// Nearest centre: distances screened in FP32.  The node's integer offset from a centre's integer part
+// is exact; the minimum image is decided on the offset less the fraction's high part (as the oracle
+// decides it on its offset; a decision that differs within an ulp of +-n/2 changes |dx| by an ulp),
+// and the offset is recomputed from the wrapped integer, so each screened component is within two
+// FP32 roundings of the exact offset and a screened squared distance within 5e-7 (relative) of the
+// FP64 one (the oracle's unfused dx*dx + dy*dy).  When every other candidate screens above
+// 1.00001 x the best + 1e-3, the best is the strict FP64 minimum and is taken as it is; otherwise (a
+// node within that margin of a Voronoi edge) the candidates inside the margin are compared in FP64
+// with the oracle's arithmetic and tie rule.  FP64 runs at 1/64 of the FP32 rate on this part, so
+// the screen decides almost every node without it.
+constexpr int kVTX = 32, kVTY = 8, kVThreads = kVTX * kVTY, kVList = 512;
+
+__global__ void __launch_bounds__(kVThreads) voronoi_tiled(Geo g, Grid G, const CRec* __restrict__ rec,
+                                                           const Header* __restrict__ h, int* __restrict__ col) {
+  __shared__ CRec s_r[kVList];
+  __shared__ float s_red[kVThreads / 32];
+  __shared__ int s_n, s_m, s_range[4];
   const int n_drops = h->n_drops;
   const int x0 = blockIdx.x * kVTX, y0 = blockIdx.y * kVTY;
   const int tid = threadIdx.y * kVTX + threadIdx.x;
+  const int w = min(kVTX, g.nx - x0), ht = min(kVTY, g.ny - y0);
   if (tid == 0) {
     // cell range of the tile's nodes, widened by 2 cells: floor(x * ncx / nx) in exact integer
     // arithmetic (the same cell as the FP64 quotient, whose rounding cannot cross an integer)
-    const long long x1 = min(x0 + kVTX - 1, g.nx - 1), y1 = min(y0 + kVTY - 1, g.ny - 1);
     s_range[0] = (int)((long long)x0 * G.ncx / g.nx) - 2;
-    s_range[1] = (int)(x1 * G.ncx / g.nx) + 2;
+    s_range[1] = (int)((long long)(x0 + w - 1) * G.ncx / g.nx) + 2;
     s_range[2] = (int)((long long)y0 * G.ncy / g.ny) - 2;
-    s_range[3] = (int)(y1 * G.ncy / g.ny) + 2;
+    s_range[3] = (int)((long long)(y0 + ht - 1) * G.ncy / g.ny) + 2;
     s_n = 0;
+    s_m = 0;
   }
   __syncthreads();
   const int cx0 = s_range[0], cy0 = s_range[2];
   const int wx = s_range[1] - cx0 + 1, wy = s_range[3] - cy0 + 1;
   bool overflow = false;
-  for (int c = tid; c < wx * wy && n_drops > 0; c += kVTX * kVTY) {
+  for (int c = tid; c < wx * wy && n_drops > 0; c += kVThreads) {
     const int jy = cy0 + c / wx, jx = cx0 + c % wx;
     int cyi = jy;
     if (g.periodic_y) cyi = ((jy % G.ncy) + G.ncy) % G.ncy;
@@ -626,55 +678,89 @@ __global__ void __launch_bounds__(kVTX * kVTY) voronoi_tiled(Geo g, Grid G, cons
       overflow = true;
       continue;
     }
-    for (int k = 0; k < n; ++k) {
-      const int d = G.citems[s + k];
-      const double cxd = G.cx[d], cyd = G.cy[d];
-      const double ix = floor(cxd), iy = floor(cyd);
-      const double fxd = cxd - ix, fyd = cyd - iy;  // exact: the centre and its floor are within one
-      const float xh = __double2float_rn(fxd), yh = __double2float_rn(fyd);
-      s_id[at + k] = d;
-      s_x[at + k] = cxd;
-      s_y[at + k] = cyd;
-      s_i[at + k] = make_int2((int)ix, (int)iy);
-      s_f[at + k] = make_float4(xh, __double2float_rn(fxd - (double)xh), yh, __double2float_rn(fyd - (double)yh));
-    }
+    for (int k = 0; k < n; ++k) s_r[at + k] = rec[s + k];
   }
-  const int any_overflow = __syncthreads_or(overflow ? 1 : 0);
+  const bool staged = !__syncthreads_or(overflow ? 1 : 0) && n_drops > 0;
+  int m = s_n;
+  if (staged && m > 0) {
+    const float hw = 0.5f * (float)(w - 1), hh = 0.5f * (float)(ht - 1);
+    const float tcx = (float)x0 + hw, tcy = (float)y0 + hh;
+    auto offset = [&](const CRec& r, float& ax, float& ay) {  // |centre - tile middle|, minimum image
+      float dx = ((float)r.i.x - tcx) + r.f.x, dy = ((float)r.i.y - tcy) + r.f.z;
+      if (dx > 0.5f * g.nx) dx -= (float)g.nx;
+      else if (dx < -0.5f * g.nx) dx += (float)g.nx;
+      if (g.periodic_y) {
+        if (dy > 0.5f * g.ny) dy -= (float)g.ny;
+        else if (dy < -0.5f * g.ny) dy += (float)g.ny;
+      }
+      ax = fabsf(dx);
+      ay = fabsf(dy);
+    };
+    float dmin = 3.0e38f;
+    for (int k = tid; k < m; k += kVThreads) {
+      float ax, ay;
+      offset(s_r[k], ax, ay);
+      dmin = fminf(dmin, ax * ax + ay * ay);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+    if ((tid & 31) == 0) s_red[tid >> 5] = dmin;
+    __syncthreads();
+    dmin = s_red[0];
+#pragma unroll
+    for (int i = 1; i < kVThreads / 32; ++i) dmin = fminf(dmin, s_red[i]);
+    const float U = (sqrtf(dmin) + sqrtf(hw * hw + hh * hh)) * 1.0001f + 0.01f;
+    constexpr int PER = kVList / kVThreads;  // each thread holds its kept records across the barrier
+    CRec kr[PER];
+    bool kk[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int k = tid + j * kVThreads;
+      kk[j] = false;
+      if (k < m) {
+        kr[j] = s_r[k];
+        float ax, ay;
+        offset(kr[j], ax, ay);
+        const float ex = fmaxf(ax - hw, 0.0f), ey = fmaxf(ay - hh, 0.0f);
+        kk[j] = ex * ex + ey * ey <= U * U;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < PER; ++j)
+      if (kk[j]) s_r[atomicAdd(&s_m, 1)] = kr[j];
+    __syncthreads();
+    m = s_m;
+  }
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-  if (x >= g.nx || y >= g.ny) return;
+  if (threadIdx.x >= w || threadIdx.y >= ht) return;
   const int n = y * g.nx + x;
   if (is_solid(g, x, y) || n_drops == 0) {
     col[n] = -1;
     return;
   }
+  const float fhx = 0.5f * g.nx, fhy = 0.5f * g.ny;
+  auto screen = [&](const CRec& r) {
+    const int dxi = x - r.i.x, dyi = y - r.i.y;
+    float dx = (float)dxi - r.f.x;
+    if (dx > fhx) dx = (float)(dxi - g.nx) - r.f.x;
+    else if (dx < -fhx) dx = (float)(dxi + g.nx) - r.f.x;
+    dx -= r.f.y;
+    float dy = (float)dyi - r.f.z;
+    if (g.periodic_y) {
+      if (dy > fhy) dy = (float)(dyi - g.ny) - r.f.z;
+      else if (dy < -fhy) dy = (float)(dyi + g.ny) - r.f.z;
+    }
+    dy -= r.f.w;
+    return dx * dx + dy * dy;
+  };
   int best_id = -1;
   bool settled = false;
-  if (!any_overflow) {
-    const int m = s_n;
-    const float fhx = 0.5f * g.nx, fhy = 0.5f * g.ny;
-    auto screen = [&](int k) {
-      const int2 ci = s_i[k];
-      const float4 f = s_f[k];
-      // minimum image decided on the offset less the fraction's high part (as the oracle decides it on
-      // its offset; a decision that differs within an ulp of +-n/2 changes |dx| by an ulp), then the
-      // offset recomputed from the wrapped integer
-      const int dxi = x - ci.x, dyi = y - ci.y;
-      float dx = (float)dxi - f.x;
-      if (dx > fhx) dx = (float)(dxi - g.nx) - f.x;
-      else if (dx < -fhx) dx = (float)(dxi + g.nx) - f.x;
-      dx -= f.y;
-      float dy = (float)dyi - f.z;
-      if (g.periodic_y) {
-        if (dy > fhy) dy = (float)(dyi - g.ny) - f.z;
-        else if (dy < -fhy) dy = (float)(dyi + g.ny) - f.z;
-      }
-      dy -= f.w;
-      return dx * dx + dy * dy;
-    };
+  if (staged) {
     float b1 = 3.0e38f, b2 = 3.0e38f;  // best and second-best screened distances
     int k1 = -1;
     for (int k = 0; k < m; ++k) {
-      const float d2 = screen(k);
+      const float d2 = screen(s_r[k]);
       if (d2 < b1) {
         b2 = b1;
         b1 = d2;
@@ -685,23 +771,23 @@ __global__ void __launch_bounds__(kVTX * kVTY) voronoi_tiled(Geo g, Grid G, cons
     }
     const float keep = b1 * 1.00001f + 1e-3f;
     if (k1 >= 0 && b2 > keep) {
-      best_id = s_id[k1];
+      best_id = s_r[k1].id;
       settled = keep < G.cw2_f;
     } else if (k1 >= 0) {
       const double px = (double)x, py = (double)y, hx = 0.5 * g.nx, hy = 0.5 * g.ny;
       double best = 0.0;
       for (int k = 0; k < m; ++k) {
-        if (screen(k) > keep) continue;
-        double dx = __dsub_rn(px, s_x[k]);
+        if (screen(s_r[k]) > keep) continue;
+        double dx = __dsub_rn(px, s_r[k].x);
         if (dx > hx) dx = __dsub_rn(dx, (double)g.nx);
         else if (dx < -hx) dx = __dadd_rn(dx, (double)g.nx);
-        double dy = __dsub_rn(py, s_y[k]);
+        double dy = __dsub_rn(py, s_r[k].y);
         if (g.periodic_y) {
           if (dy > hy) dy = __dsub_rn(dy, (double)g.ny);
           else if (dy < -hy) dy = __dadd_rn(dy, (double)g.ny);
         }
         const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-        const int d = s_id[k];
+        const int d = s_r[k].id;
         if (best_id < 0 || d2 < best || (d2 == best && d < best_id)) {
           best = d2;
           best_id = d;
@@ -714,17 +800,26 @@ __global__ void __launch_bounds__(kVTX * kVTY) voronoi_tiled(Geo g, Grid G, cons
   col[n] = best_id;
 }
 
-// ---------------------------------------------------------------- links (D6)
-
+// Inserts b into a's adjacency set unless it is there: the set is read first and the first empty
+// slot claimed with one compare-and-swap (re-read when another insert took it), so an insert costs
+// one atomic when it does not race.
 __device__ __forceinline__ void adj_insert(int* adj, int* deg, int a, int b, int* err) {
   int* slots = adj + (long long)a * kMaxDeg;
-  for (int k = 0; k < kMaxDeg; ++k) {
-    const int v = atomicCAS(slots + k, -1, b);
-    if (v == -1) {
+  int k = 0;
+  while (k < kMaxDeg) {
+    const int v = *reinterpret_cast<volatile int*>(slots + k);
+    if (v == b) return;
+    if (v != -1) {
+      ++k;
+      continue;
+    }
+    const int old = atomicCAS(slots + k, -1, b);
+    if (old == -1) {
       atomicAdd(deg + a, 1);
       return;
     }
-    if (v == b) return;
+    if (old == b) return;
+    ++k;  // the slot was taken meanwhile by another value: the next one
   }
   atomicOr(err, kErrDegree);
 }
@@ -738,6 +833,7 @@ __global__ void voronoi_links(Geo g, const int* __restrict__ col, int* adj, int*
   // corners in cyclic order: 00, 10, 11, 01
   const int c[4] = {col[y * g.nx + x], col[y * g.nx + x1], col[y1 * g.nx + x1], col[y1 * g.nx + x]};
   if (c[0] < 0 || c[1] < 0 || c[2] < 0 || c[3] < 0) return;
+  if (c[0] == c[1] && c[1] == c[2] && c[2] == c[3]) return;
   int dist[4], k = 0;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -1021,6 +1117,47 @@ int read_header(lb_handle* h, const void* ws, Header* out) {
   return LB_OK;
 }
 
+// Enqueues one droplet analysis of the current state on stream s (no host synchronisation).
+cudaError_t enqueue_analysis(const lb_handle* h, const DView& v, const DLayout& L, const Header& hdr, double threshold,
+                             int max_drops, cudaStream_t s) {
+  const Geo g{h->p.nx, h->p.ny, h->p.periodic_y, h->cfg.mask};
+  double* stage = static_cast<double*>(h->buf[h->cur ^ 1]);  // rho1 is plane 0 of the fields
+  const int N = (int)L.N;  // nx * ny fits in 31 bits (lb_init)
+  const int T = 256;
+  // the per-droplet kernels run grid-stride over the count the labelling writes into the header
+  auto capped = [](unsigned blocks) { return blocks < kGridCap ? blocks : kGridCap; };
+  const unsigned per_drop = capped(nb(max_drops, T)), per_drop_warps = capped(nb((long long)max_drops * 32, T));
+  const unsigned reset_blocks =
+      capped(nb((long long)max_drops * kMaxDeg > L.ncell ? (long long)max_drops * kMaxDeg : L.ncell, T));
+  int* err = &v.hdr->err;
+  cudaError_t e = launch_mode(h->p.precision, MODE_RHO1, h->cfg, h->buf[h->cur], nullptr, stage, s);
+  if (e != cudaSuccess) return e;
+  drop_reset<<<reset_blocks, T, 0, s>>>(v.hdr, hdr, v.cnt, v.sx, v.sy, v.adj, v.deg, v.ccount, v.cfill, L.ncell);
+  // labels (D1-D3): tile-local union-find, unions across tile borders, roots and their ids
+  const int ncol = (h->p.nx + kLT - 1) / kLT, nrow = (h->p.ny + kLT - 1) / kLT;
+  label_local<<<dim3((unsigned)ncol, (unsigned)nrow), kLThreads, 0, s>>>(stage, threshold, g, v.lab, err);
+  label_border<<<nb((long long)h->p.ny * ncol + (long long)h->p.nx * nrow, T), T, 0, s>>>(g, ncol, nrow, v.lab, err);
+  label_flatten<<<L.nblk, kScanBlock, 0, s>>>(N, v.lab, v.rmask, v.blk, err);
+  label_count<<<1, kScanBlock, 0, s>>>(v.blk, L.nblk, v.hdr, max_drops);
+  const int n_words = (N + 31) / 32;
+  warp_offsets<<<nb(n_words, T), T, 0, s>>>(n_words, v.rmask, v.blk, v.woff);
+  // centres (D4) and the cell grid of the centres
+  centre_sums<<<nb(N, T), T, 0, s>>>(g, v.lab, v.rmask, v.woff, v.hdr, v.did, v.root, v.cnt, v.sx, v.sy);
+  centre_final<<<per_drop, T, 0, s>>>(g, v.hdr, v.root, v.cnt, v.sx, v.sy, v.cx, v.cy, L.ncx, L.ncy, v.ccount, v.lcount,
+                                      v.crec_id);
+  cell_fill<<<1, kScanBlock, 0, s>>>(v.hdr, L.ncell, v.ccount, v.cstart, v.lcount, v.cfill, v.citems, v.crec_id,
+                                     v.crec);
+  // colours (D5) and links (D6)
+  const Grid G = grid_of(v, L, h->p);
+  voronoi_tiled<<<dim3((unsigned)((h->p.nx + kVTX - 1) / kVTX), (unsigned)((h->p.ny + kVTY - 1) / kVTY)),
+                  dim3(kVTX, kVTY), 0, s>>>(g, G, v.crec, v.hdr, v.col);
+  voronoi_links<<<nb(N, T), T, 0, s>>>(g, v.col, v.adj, v.deg, err);
+  adj_sort<<<per_drop_warps, T, 0, s>>>(v.hdr, v.adj, v.deg, v.lcount);
+  links_count<<<1, kScanBlock, 0, s>>>(v.hdr, v.lcount, v.loff);
+  links_write<<<per_drop, T, 0, s>>>(v.hdr, v.adj, v.deg, v.loff, v.links, L.max_links);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 extern "C" {
@@ -1039,9 +1176,6 @@ int lb_droplets(lb_handle* h, double threshold, int max_drops, void* d_ws, size_
     return dfail(h, LB_ENOSPACE, "droplet workspace too small, misaligned or max_drops < 1");
   if (!(threshold == threshold)) return dfail(h, LB_EINVAL, "threshold is NaN");
   const DView v = view(d_ws, L);
-  const Geo g{h->p.nx, h->p.ny, h->p.periodic_y, h->cfg.mask};
-  cudaStream_t s = h->stream;
-  double* stage = static_cast<double*>(h->buf[h->cur ^ 1]);  // rho1 is plane 0 of the fields
   Header hdr{};
   hdr.max_drops = max_drops;
   hdr.nx = h->p.nx;
@@ -1049,37 +1183,36 @@ int lb_droplets(lb_handle* h, double threshold, int max_drops, void* d_ws, size_
   hdr.periodic_y = h->p.periodic_y;
   hdr.ncx = L.ncx;
   hdr.ncy = L.ncy;
-  const int N = (int)L.N;  // nx * ny fits in 31 bits (lb_init)
-  const int T = 256;
-  // per-droplet kernels run grid-stride over the count the labelling wrote into the header
-  auto capped = [](unsigned blocks) { return blocks < kGridCap ? blocks : kGridCap; };
-  const unsigned per_drop = capped(nb(max_drops, T)), per_drop_warps = capped(nb((long long)max_drops * 32, T));
-  const unsigned reset_blocks =
-      capped(nb((long long)max_drops * kMaxDeg > L.ncell ? (long long)max_drops * kMaxDeg : L.ncell, T));
-  int* err = &v.hdr->err;
-  cudaError_t e = fields_into(h, stage);
-  if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets fields", e);
-  drop_reset<<<reset_blocks, T, 0, s>>>(v.hdr, hdr, v.cnt, v.sx, v.sy, v.adj, v.deg, v.ccount, v.cfill, L.ncell);
-  // labels (D1-D3): tile-local union-find, unions across tile borders, roots and their ids
-  const int ncol = (h->p.nx + kLT - 1) / kLT, nrow = (h->p.ny + kLT - 1) / kLT;
-  label_local<<<dim3((unsigned)ncol, (unsigned)nrow), kLThreads, 0, s>>>(stage, threshold, g, v.lab, err);
-  label_border<<<nb((long long)h->p.ny * ncol + (long long)h->p.nx * nrow, T), T, 0, s>>>(g, ncol, nrow, v.lab, err);
-  label_flatten<<<L.nblk, kScanBlock, 0, s>>>(N, v.lab, v.did, v.blk, err);
-  label_count<<<1, kScanBlock, 0, s>>>(v.blk, L.nblk, v.hdr, max_drops);
-  label_ids<<<L.nblk, kScanBlock, 0, s>>>(N, v.did, v.blk, v.root, max_drops);
-  // centres (D4) and the cell grid of the centres
-  centre_sums<<<nb(N, T), T, 0, s>>>(g, v.lab, v.did, v.root, v.hdr, v.cnt, v.sx, v.sy);
-  centre_final<<<per_drop, T, 0, s>>>(g, v.hdr, v.root, v.cnt, v.sx, v.sy, v.cx, v.cy, L.ncx, L.ncy, v.ccount, v.lcount);
-  cell_fill<<<1, kScanBlock, 0, s>>>(v.hdr, L.ncell, v.ccount, v.cstart, v.lcount, v.cfill, v.citems);
-  // colours (D5) and links (D6)
-  const Grid G = grid_of(v, L, h->p);
-  voronoi_tiled<<<dim3((unsigned)((h->p.nx + kVTX - 1) / kVTX), (unsigned)((h->p.ny + kVTY - 1) / kVTY)),
-                  dim3(kVTX, kVTY), 0, s>>>(g, G, v.hdr, v.col);
-  voronoi_links<<<nb(N, T), T, 0, s>>>(g, v.col, v.adj, v.deg, err);
-  adj_sort<<<per_drop_warps, T, 0, s>>>(v.hdr, v.adj, v.deg, v.lcount);
-  links_count<<<1, kScanBlock, 0, s>>>(v.hdr, v.lcount, v.loff);
-  links_write<<<per_drop, T, 0, s>>>(v.hdr, v.adj, v.deg, v.loff, v.links, L.max_links);
-  e = cudaGetLastError();
+  // The launches from the rho_1 pass to the link list depend only on the lattice, the workspace, the
+  // droplet bound, the threshold and the current buffer: they are captured once per such key into a
+  // CUDA graph and replayed (four keys are kept, replaced in turn).
+  lb_handle::DropGraph* dg = nullptr;
+  for (auto& c : h->dgraph)
+    if (c.exec && c.ws == d_ws && c.max_drops == max_drops && c.threshold == threshold && c.cur == h->cur) dg = &c;
+  if (!dg) {
+    dg = &h->dgraph[h->dgraph_next];
+    h->dgraph_next = (h->dgraph_next + 1) % 4;
+    if (dg->exec) cudaGraphExecDestroy(dg->exec);
+    *dg = lb_handle::DropGraph{};
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t e1 = enqueue_analysis(h, v, L, hdr, threshold, max_drops, h->cap);
+      e = cudaStreamEndCapture(h->cap, &graph);
+      if (e1 != cudaSuccess) e = e1;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&dg->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      dg->exec = nullptr;
+      return dfail(h, LB_ECUDA, "lb_droplets capture", e);
+    }
+    dg->ws = d_ws;
+    dg->max_drops = max_drops;
+    dg->threshold = threshold;
+    dg->cur = h->cur;
+  }
+  const cudaError_t e = cudaGraphLaunch(dg->exec, h->stream);
   if (e != cudaSuccess) return dfail(h, LB_ECUDA, "lb_droplets", e);
   Header got{};
   if (int rc = read_header(h, v.hdr, &got)) return rc;

@@ -172,6 +172,14 @@ struct lb_handle {
   int cur = 0;
   long long step = 0;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  // captured droplet analyses (lb_droplets), keyed by what their launches bake in
+  struct DropGraph {
+    cudaGraphExec_t exec = nullptr;
+    const void* ws = nullptr;
+    int max_drops = 0, cur = -1;
+    double threshold = 0.0;
+  } dgraph[4];
+  int dgraph_next = 0;
   int tile = 0;  // step-kernel tile candidate (see lb_autotune)
   char err[512] = "no error";
 };

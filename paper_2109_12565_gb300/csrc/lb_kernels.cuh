@@ -1029,6 +1029,32 @@ cudaError_t launch_tile_kernel(const dim3& grid, const SF<S>* in, SF<S>* out, co
   return cudaGetLastError();
 }
 
+inline dim3 rows_grid(const StepCfg& c) { return dim3((unsigned)((c.nx + 127) / 128), (unsigned)c.ny, 1u); }
+
+// rho_1 of every node (nx*ny doubles; rho_w at solid nodes) with the arithmetic of the field mode:
+// phase A's packed sum of component 1's nine populations (lane x; lane y carries zeros), plus the
+// shift in shifted storage, widened to double.  The same bits as plane 0 of MODE_FIELDS, from 9 of
+// the 27 planes.
+template <class S, bool SHIFT>
+__global__ void lb_rho1_kernel(const SF<S>* __restrict__ buf, double* __restrict__ out, const KParams<SC<S>> kp) {
+  using C = SC<S>;
+  const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
+  if (gx >= kp.nx || gy >= kp.ny) return;
+  const int n = gy * kp.nx + gx;
+  bool solid = kp.mask != nullptr && kp.mask[n] != 0;
+  if (!kp.periodic_y && (gy == 0 || gy == kp.ny - 1)) solid = true;
+  if (solid) {
+    out[n] = kp.rho_w_d[0];
+    return;
+  }
+  const SF<S>* src = buf + (gy * kp.pitch + gx);
+  V2<C> d = splat<C>(C(0));
+#pragma unroll
+  for (int i = 0; i < 9; ++i) d = p_acc(d, v2<C>(C(ld_pop<false>(src + i * kp.plane)), C(0)));
+  const C r1 = SHIFT ? d.x + kp.rho_bar[0] : d.x;
+  out[n] = (double)r1;
+}
+
 template <class S> struct MinBlocks;
 template <> struct MinBlocks<double> { static constexpr int value = 2; };
 template <> struct MinBlocks<float> { static constexpr int value = 3; };
@@ -1049,6 +1075,9 @@ cudaError_t launch_impl(int mode, const StepCfg& c, const void* fin, void* fout,
       return launch_tile_kernel<S, MODE_OBS, T::TX, T::TY, T::BY, 1, SHIFT>(grid, in, out, kp, aux, s);
     case MODE_FIELDS:
       return launch_tile_kernel<S, MODE_FIELDS, T::TX, T::TY, T::BY, 1, SHIFT>(grid, in, out, kp, aux, s);
+    case MODE_RHO1:
+      lb_rho1_kernel<S, SHIFT><<<rows_grid(c), 128, 0, s>>>(in, aux, kp);
+      return cudaGetLastError();
     default:
       return cudaErrorInvalidValue;
   }
@@ -1060,7 +1089,5 @@ cudaError_t launch_step_shape(const StepCfg& c, const void* fin, void* fout, cud
                                                                static_cast<const SF<S>*>(fin), static_cast<SF<S>*>(fout),
                                                                make_kparams<SC<S>>(c), nullptr, s);
 }
-
-inline dim3 rows_grid(const StepCfg& c) { return dim3((unsigned)((c.nx + 127) / 128), (unsigned)c.ny, 1u); }
 
 }  // namespace tlb

@@ -42,7 +42,7 @@ def _compare(g, d, params, mask=None, threshold=BTH):
     return o
 
 
-@pytest.mark.parametrize("precision", [lb.LB_FP64, lb.LB_FP32_SHIFTED, lb.LB_FP32_FP16T])
+@pytest.mark.parametrize("precision", [lb.LB_FP64, lb.LB_FP32_SHIFTED, lb.LB_FP32_FP16T, lb.LB_DF64])
 def test_emulsion_64x64_matches_oracle(precision):
     w = I.emulsion_small()
     g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0, precision=precision)
@@ -98,6 +98,20 @@ def test_percolation_clusters_across_tiles(nx, ny, periodic, p):
     if p > 0.6:  # above the site-percolation threshold: the largest cluster crosses the tile grid
         ys, xs = np.nonzero(d["label"] == np.argmax(d["size"]))
         assert np.ptp(xs) > 64 and np.ptp(ys) > 32
+
+
+def test_replayed_analyses_follow_the_state():
+    """lb_droplets replays a captured launch sequence per (workspace, droplet bound, threshold, current
+    buffer), four kept: analyses with steps in between, alternating workspaces, three thresholds and
+    both buffer parities (more keys than kept) each match the oracle on the current state."""
+    w = I.emulsion_small(nx=96, ny=64, n_drops=5, R=7.0)
+    g = lb.Lattice(w.params, w.rho1, w.rho2, w.T0)
+    prev = None
+    for steps, th in [(0, BTH), (1, BTH), (5, 0.7), (1, BTH), (2, 0.7), (1, 0.9), (3, BTH), (1, 0.7), (0, BTH)]:
+        g.step(steps)
+        d = g.droplets(th)
+        _compare(g, d, w.params, threshold=th)
+        prev, d = d, None  # keep the previous workspace alive, so that the next one lands elsewhere
 
 
 def test_degenerate_cases():
