@@ -52,16 +52,20 @@ __device__ __forceinline__ float df_two_prod(float a, float b, float& e) {
   return p;
 }
 
-// a + b, accurate also under cancellation: both parts are summed error-free.
+// a + b: the leading parts summed error-free, the low parts in FP32, one renormalisation (11
+// operations).  The only rounding beyond the final one is that of a.lo + b.lo, at most
+// 2^-24 |a.lo + b.lo| <= 2^-48 (|a| + |b|): the error is bounded relative to the operands rather than
+// to the sum, which under cancellation is larger than the summands' own rounding in FP64 by a small
+// factor only (the step's quantities are O(1) and the tolerance is absolute).  The variant that also
+// sums the low parts error-free costs 20 operations; the whole step measured 13% slower with it and
+// 5.4e-14 instead of 7.3e-14 from the FP64 oracle after 1000 steps of the 64 x 64 emulsion.
 __device__ __forceinline__ df df_add(df a, df b) {
-  float e1, e2;
-  float s = df_two_sum(a.hi, b.hi, e1);
-  const float t = df_two_sum(a.lo, b.lo, e2);
-  e1 = __fadd_rn(e1, t);
-  s = df_fast_two_sum(s, e1, e1);
-  e1 = __fadd_rn(e1, e2);
-  s = df_fast_two_sum(s, e1, e1);
-  return df(s, e1);
+  float e;
+  const float s = df_two_sum(a.hi, b.hi, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  float l;
+  const float h = df_fast_two_sum(s, e, l);
+  return df(h, l);
 }
 __device__ __forceinline__ df df_neg(df a) { return df(-a.hi, -a.lo); }
 __device__ __forceinline__ df df_mul(df a, df b) {
@@ -119,17 +123,7 @@ __device__ __forceinline__ float2 hi2(df2 a) { return make_float2(a.x.hi, a.y.hi
 __device__ __forceinline__ float2 lo2(df2 a) { return make_float2(a.x.lo, a.y.lo); }
 __device__ __forceinline__ df2 make_df2(float2 h, float2 l) { return df2{df(h.x, l.x), df(h.y, l.y)}; }
 
-__device__ __forceinline__ df2 p_add(df2 a, df2 b) {
-  float2 e1, e2;
-  float2 s = f2_two_sum(hi2(a), hi2(b), e1);
-  const float2 t = f2_two_sum(lo2(a), lo2(b), e2);
-  e1 = f2_add(e1, t);
-  s = f2_fast_two_sum(s, e1, e1);
-  e1 = f2_add(e1, e2);
-  s = f2_fast_two_sum(s, e1, e1);
-  return make_df2(s, e1);
-}
-__device__ __forceinline__ df2 p_acc(df2 a, df2 b) {  // df_add_same_sign per lane, packed
+__device__ __forceinline__ df2 p_add(df2 a, df2 b) {  // df_add per lane, packed
   float2 e;
   const float2 s = f2_two_sum(hi2(a), hi2(b), e);
   e = f2_add(e, f2_add(lo2(a), lo2(b)));
@@ -137,6 +131,7 @@ __device__ __forceinline__ df2 p_acc(df2 a, df2 b) {  // df_add_same_sign per la
   const float2 h = f2_fast_two_sum(s, e, l);
   return make_df2(h, l);
 }
+__device__ __forceinline__ df2 p_acc(df2 a, df2 b) { return p_add(a, b); }
 __device__ __forceinline__ df2 p_sub(df2 a, df2 b) {
   const float2 bh = hi2(b), bl = lo2(b);
   return p_add(a, make_df2(make_float2(-bh.x, -bh.y), make_float2(-bl.x, -bl.y)));
@@ -166,17 +161,7 @@ __device__ __forceinline__ df2 p_fma(df2 a, df2 b, df2 c) {
   return make_df2(h, l);
 }
 __device__ __forceinline__ df s_add(df a, df b) { return df_add(a, b); }
-// a + b for operands of one sign: one two-sum of the leading parts, the low parts summed in FP32; the
-// error stays below 2^-47 |a + b| when no cancellation can occur.
-__device__ __forceinline__ df df_add_same_sign(df a, df b) {
-  float e;
-  const float s = df_two_sum(a.hi, b.hi, e);
-  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-  float l;
-  const float h = df_fast_two_sum(s, e, l);
-  return df(h, l);
-}
-__device__ __forceinline__ df s_acc(df a, df b) { return df_add_same_sign(a, b); }
+__device__ __forceinline__ df s_acc(df a, df b) { return df_add(a, b); }
 __device__ __forceinline__ df s_mul(df a, df b) { return df_mul(a, b); }
 __device__ __forceinline__ df s_fma(df a, df b, df c) { return df_fma(a, b, c); }
 
