@@ -123,6 +123,19 @@ __device__ __forceinline__ float2 hi2(df2 a) { return make_float2(a.x.hi, a.y.hi
 __device__ __forceinline__ float2 lo2(df2 a) { return make_float2(a.x.lo, a.y.lo); }
 __device__ __forceinline__ df2 make_df2(float2 h, float2 l) { return df2{df(h.x, l.x), df(h.y, l.y)}; }
 
+// In shared memory a pair is kept as (high parts of both lanes, low parts of both lanes): one 16-byte
+// load then gives the two register pairs the packed instructions take.
+struct __align__(16) df2s {
+  float2 hi, lo;
+  __device__ __forceinline__ operator df2() const { return make_df2(hi, lo); }
+  __device__ __forceinline__ df2s& operator=(const df2& v) {
+    hi = hi2(v);
+    lo = lo2(v);
+    return *this;
+  }
+};
+template <> struct SmemPairT<df> { using type = df2s; };
+
 __device__ __forceinline__ df2 p_add(df2 a, df2 b) {  // df_add per lane, packed
   float2 e;
   const float2 s = f2_two_sum(hi2(a), hi2(b), e);

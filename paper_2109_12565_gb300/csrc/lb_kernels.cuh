@@ -239,10 +239,15 @@ __device__ __forceinline__ double s_mul(double a, double b) { return __dmul_rn(a
 __device__ __forceinline__ double s_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 template <class C> __device__ __forceinline__ C s_acc(C a, C b) { return s_add(a, b); }
 
+// The shared-memory form of a lane pair: the pair itself, unless a form keeps it in another order
+// (converting on every load and store).
+template <class C> struct SmemPairT { using type = V2<C>; };
+template <class C> using SmemPair = typename SmemPairT<C>::type;
+
 template <class C, int TX, int TY, bool NEED_T> struct alignas(16) TileSmem {
   static constexpr int RX = TX + 4, RY = TY + 4;
-  V2<C> rho[RY][RX];  // density deviations rho_l - rho_bar_l (rho_bar = 0 in FP64), components interleaved
-  V2<C> psi[RY][RX];
+  SmemPair<C> rho[RY][RX];  // density deviations rho_l - rho_bar_l (rho_bar = 0 in FP64), components interleaved
+  SmemPair<C> psi[RY][RX];
   C jx[TY][TX], jy[TY][TX];  // bare momentum of the tile's own nodes
   C T[NEED_T ? RY : 1][NEED_T ? RX : 1];
   unsigned char solid[RY][RX];
@@ -703,12 +708,16 @@ __device__ __forceinline__ void node_collide(const KParams<C>& kp, const C f[9],
 template <class S, class C, bool FAST, int RX>
 __device__ __forceinline__ void push_store(SF<S>* __restrict__ fout, const KParams<C>& kp, int idx, int gx, int gy,
                                            const C post[27], const unsigned char (*solid)[RX], int cx, int cy, C r1,
-                                           C r2) {
+                                           C r2, bool fast_store = false) {
   using F = SF<S>;
   using G = SG<S>;
   const int nx = kp.nx, ny = kp.ny, pitch = kp.pitch, plane = kp.plane;
   G* __restrict__ gout = thermal_planes<S>(fout, plane);
-  if constexpr (FAST) {
+  // a form with one phase-B instance takes the constant-offset stores at run time on the tiles that
+  // allow them (fast_store: no solid node around the tile and no periodic wrap); the others decide at
+  // compile time
+  if constexpr (FAST || Storage<S>::kFastPath) fast_store = FAST;
+  if (fast_store) {
     F* dst = fout + idx;
     G* gdst = gout + idx;
 #pragma unroll
@@ -757,8 +766,9 @@ template <class C, bool SHIFT, class SMT>
 __device__ __forceinline__ NodeMoments<C> node_moments(const SMT& sm, const KParams<C>& kp, int tx, int ty,
                                                        const C g[9]) {
   NodeMoments<C> m;
-  m.dr1 = sm.rho[ty + 2][tx + 2].x;
-  m.dr2 = sm.rho[ty + 2][tx + 2].y;
+  const V2<C> dr = sm.rho[ty + 2][tx + 2];
+  m.dr1 = dr.x;
+  m.dr2 = dr.y;
   m.r1 = SHIFT ? m.dr1 + kp.rho_bar[0] : m.dr1;
   m.r2 = SHIFT ? m.dr2 + kp.rho_bar[1] : m.dr2;
   m.dT = C(0);
@@ -776,7 +786,8 @@ __device__ __forceinline__ NodeMoments<C> node_moments(const SMT& sm, const KPar
 template <class S, class C, bool SHIFT, bool FAST, class SMT>
 __device__ __forceinline__ C step_finish(SF<S>* __restrict__ fout, const KParams<C>& kp, const SMT& sm,
                                          const C f[9], const C h[9], const C g[9], const NodeMoments<C>& m,
-                                         int tx, int ty, int gx, int gy, int idx, V2<C> Fx2, V2<C> Fyp) {
+                                         int tx, int ty, int gx, int gy, int idx, V2<C> Fx2, V2<C> Fyp,
+                                         bool fast_store = false) {
   const V2<C> Fy2 = buoyant_fy<C>(kp, Fyp, v2<C>(m.r1, m.r2), m.T);
   const C Fx[2] = {Fx2.x, Fx2.y}, Fy[2] = {Fy2.x, Fy2.y};
   C i1, i2, inv_rho, ux, uy, uHx, uHy;
@@ -784,7 +795,7 @@ __device__ __forceinline__ C step_finish(SF<S>* __restrict__ fout, const KParams
   node_velocities<C>(m.jx, m.jy, inv_rho, Fx, Fy, ux, uy, uHx, uHy);
   C post[27];
   node_collide<C, SHIFT>(kp, f, h, g, m.r1, m.r2, m.dr1, m.dr2, m.T, m.dT, ux, uy, i1, i2, Fx, Fy, uHx, uHy, post);
-  push_store<S, C, FAST>(fout, kp, idx, gx, gy, post, sm.solid, tx + 2, ty + 2, m.r1, m.r2);
+  push_store<S, C, FAST>(fout, kp, idx, gx, gy, post, sm.solid, tx + 2, ty + 2, m.r1, m.r2, fast_store);
   return uHy * m.T;
 }
 
@@ -793,7 +804,7 @@ __device__ __forceinline__ C step_finish(SF<S>* __restrict__ fout, const KParams
 template <class S, class C, bool SHIFT, int MODE, bool FAST, int TX, int TY, int BY, class Src>
 __device__ __forceinline__ void tile_phase_b(const Src& pop, SF<S>* __restrict__ fout, const KParams<C>& kp, int x0, int y0,
                                              const TileSmem<C, TX, TY, mode_needs_T(MODE)>& sm, double* __restrict__ aux,
-                                             double acc[kObsSlots], C* nu = nullptr) {
+                                             double acc[kObsSlots], C* nu = nullptr, bool fast_store = false) {
   const int nx = kp.nx, ny = kp.ny, pitch = kp.pitch, plane = kp.plane;
 #pragma unroll 1
   for (int k = 0; k < TY / BY; ++k) {
@@ -831,7 +842,7 @@ __device__ __forceinline__ void tile_phase_b(const Src& pop, SF<S>* __restrict__
     V2<C> fx2, fyp2, q0, q1, q2, q3, q4;
     node_force_pair<C>(sm, kp, cx, cy, v2<C>(r1, r2), fx2, fyp2, q0, q1, q2, q3, q4);
     if constexpr (mode_steps(MODE)) {
-      const C uyT = step_finish<S, C, SHIFT, FAST>(fout, kp, sm, f, h, g, m, tx, ty, gx, gy, idx, fx2, fyp2);
+      const C uyT = step_finish<S, C, SHIFT, FAST>(fout, kp, sm, f, h, g, m, tx, ty, gx, gy, idx, fx2, fyp2, fast_store);
       if constexpr (MODE == MODE_STEP_NU) *nu = s_add(*nu, uyT);  // in the arithmetic precision
       continue;
     }
@@ -900,7 +911,7 @@ __device__ __forceinline__ void tile_step(const SF<S>* __restrict__ fin, SF<S>* 
       return;
     }
   }
-  tile_phase_b<S, C, SHIFT, MODE, false, TX, TY, BY>(pop, fout, kp, x0, y0, sm, aux, acc, nu);
+  tile_phase_b<S, C, SHIFT, MODE, false, TX, TY, BY>(pop, fout, kp, x0, y0, sm, aux, acc, nu, fast);
 }
 
 // Block-wide deterministic sum of the observable accumulators into aux[slot * kObsSlots + v].
