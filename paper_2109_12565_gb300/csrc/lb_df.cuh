@@ -201,7 +201,7 @@ template <> __host__ __device__ constexpr df wq<df>(int i) {
 }
 
 template <> struct Tile<df> { static constexpr int TX = 32, TY = 16, BY = 8; };
-template <> struct MinBlocks<df> { static constexpr int value = 2; };
+template <> struct MinBlocks<df> { static constexpr int value = 3; };
 
 // 1 / x: an FP32 reciprocal refined by two Newton steps y <- y + y (1 - x y), the residual taken in
 // double-float; relative error about 2^-47.
