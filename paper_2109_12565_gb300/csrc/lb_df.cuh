@@ -173,6 +173,41 @@ __device__ __forceinline__ df2 p_fma(df2 a, df2 b, df2 c) {
   const float2 h = f2_fast_two_sum(sh, t, l);
   return make_df2(h, l);
 }
+// Nine-term sums: the high parts accumulated by two-sums, the two-sums' errors and the low parts summed
+// in FP32, one renormalisation at the end (8 operations a term against the 11 of the add).  Every
+// rounding beyond the final one is an FP32 rounding of a partial sum of low-order terms, below
+// 2^-24 of it: the error regime of the add.
+template <> struct Sum9<df2> {
+  __device__ __forceinline__ static df2 of(const df2 u[9]) {
+    float2 s = hi2(u[0]), err = make_float2(0.0f, 0.0f), lo = lo2(u[0]);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+      float2 e;
+      s = f2_two_sum(s, hi2(u[i]), e);
+      err = f2_add(err, e);
+      lo = f2_add(lo, lo2(u[i]));
+    }
+    float2 l;
+    const float2 h = f2_fast_two_sum(s, f2_add(err, lo), l);
+    return make_df2(h, l);
+  }
+};
+template <> struct SSum9<df> {
+  __device__ __forceinline__ static df of(const df u[9]) {
+    float s = u[0].hi, err = 0.0f, lo = u[0].lo;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+      float e;
+      s = df_two_sum(s, u[i].hi, e);
+      err = __fadd_rn(err, e);
+      lo = __fadd_rn(lo, u[i].lo);
+    }
+    float l;
+    const float h = df_fast_two_sum(s, __fadd_rn(err, lo), l);
+    return df(h, l);
+  }
+};
+
 __device__ __forceinline__ df s_add(df a, df b) { return df_add(a, b); }
 __device__ __forceinline__ df s_acc(df a, df b) { return df_add(a, b); }
 __device__ __forceinline__ df s_mul(df a, df b) { return df_mul(a, b); }

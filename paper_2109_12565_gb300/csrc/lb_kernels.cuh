@@ -238,6 +238,26 @@ __device__ __forceinline__ double s_add(double a, double b) { return __dadd_rn(a
 __device__ __forceinline__ double s_mul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double s_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 template <class C> __device__ __forceinline__ C s_acc(C a, C b) { return s_add(a, b); }
+// Sum of the nine populations of a density or of a node's thermal set, in a fixed order: for FP32 and
+// FP64 the adds ((u[0] + u[1]) + u[2]) + ... + u[8]; a compound form may specialise it.
+template <class V> struct Sum9 {
+  __device__ __forceinline__ static V of(const V u[9]) {
+    V d = u[0];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) d = p_acc(d, u[i]);
+    return d;
+  }
+};
+template <class V> __device__ __forceinline__ V p_sum9(const V u[9]) { return Sum9<V>::of(u); }
+template <class C> struct SSum9 {
+  __device__ __forceinline__ static C of(const C u[9]) {
+    C d = u[0];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) d = s_acc(d, u[i]);
+    return d;
+  }
+};
+template <class C> __device__ __forceinline__ C s_sum9(const C u[9]) { return SSum9<C>::of(u); }
 
 // The shared-memory form of a lane pair: the pair itself, unless a form keeps it in another order
 // (converting on every load and store).
@@ -436,9 +456,7 @@ __device__ __forceinline__ bool tile_phase_a(const SF<S>* __restrict__ fin, cons
       V2<C> u[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) u[i] = v2<C>(C(ld_pop<CG>(src + i * plane)), C(ld_pop<CG>(src + (9 + i) * plane)));
-      V2<C> d = splat<C>(C(0));
-#pragma unroll
-      for (int i = 0; i < 9; ++i) d = p_acc(d, u[i]);
+      const V2<C> d = p_sum9(u);
       sm.rho[ry][rx] = d;
       sm.psi[ry][rx] = psi_exp_pair<C>(p_add(d, v2<C>(rb0, rb1)), kp.rho0, kp.inv_rho0);
       if (rx >= 2 && rx < TX + 2 && ry >= 2 && ry < TY + 2) {
@@ -602,8 +620,10 @@ template <class C> __device__ __forceinline__ void three_reciprocals(C r1, C r2,
   const C rho = s_add(r1, r2);
   const C p12 = s_mul(r1, r2);
   const C inv = recip<C>(s_mul(p12, rho));
-  i1 = s_mul(s_mul(r2, rho), inv);
-  i2 = s_mul(s_mul(r1, rho), inv);
+  // i1 = (r2 rho) inv and i2 = (r1 rho) inv as one lane pair (each lane the two scalar products)
+  const V2<C> q = p_mul(p_mul(v2<C>(r2, r1), splat<C>(rho)), splat<C>(inv));
+  i1 = q.x;
+  i2 = q.y;
   irho = s_mul(p12, inv);
 }
 
@@ -611,10 +631,14 @@ template <class C> __device__ __forceinline__ void three_reciprocals(C r1, C r2,
 template <class C>
 __device__ __forceinline__ void node_velocities(C jx, C jy, C inv_rho, const C Fx[2], const C Fy[2], C& ux, C& uy,
                                                 C& uHx, C& uHy) {
-  ux = s_mul(jx, inv_rho);
-  uy = s_mul(jy, inv_rho);
-  uHx = s_fma(s_mul(C(0.5), s_add(Fx[0], Fx[1])), inv_rho, ux);
-  uHy = s_fma(s_mul(C(0.5), s_add(Fy[0], Fy[1])), inv_rho, uy);
+  // x and y as one lane pair: each lane the scalar operations u = j / rho, u^(H) = (F / 2) / rho + u
+  const V2<C> u = p_mul(v2<C>(jx, jy), splat<C>(inv_rho));
+  const V2<C> f = p_add(v2<C>(Fx[0], Fy[0]), v2<C>(Fx[1], Fy[1]));
+  const V2<C> uh = p_fma(p_mul(splat<C>(C(0.5)), f), splat<C>(inv_rho), u);
+  ux = u.x;
+  uy = u.y;
+  uHx = uh.x;
+  uHy = uh.y;
 }
 
 // BGK relaxation of the 27 populations of one node (Eqs. BGK, LBMg, Teq); in shifted storage the
@@ -638,13 +662,25 @@ __device__ __forceinline__ void collide_fluid(const KParams<C>& kp, const C f[9]
   V cu[9];
   cu[1] = ulx, cu[2] = uly, cu[5] = p_add(ulx, uly), cu[6] = p_sub(uly, ulx);
   V feq[9];
-  feq[0] = p_mul(splat<C>(wq<C>(0)), p_fma(r, nusq, base));
+  if constexpr (SHIFT) {
+    feq[0] = p_mul(splat<C>(wq<C>(0)), p_fma(r, nusq, base));
+  } else {
+    // without a shift f^eq = w_i rho (1 + P_i) = A + A P_i, A = w_i rho once per weight class
+    const V a0 = p_mul(splat<C>(wq<C>(0)), r);
+    feq[0] = p_fma(a0, nusq, a0);
+  }
+  const V a1 = SHIFT ? r : p_mul(splat<C>(wq<C>(1)), r), a5 = SHIFT ? r : p_mul(splat<C>(wq<C>(5)), r);
 #pragma unroll
   for (int i = 1; i < 9; ++i) {
     const bool odd = (i == 3 || i == 4 || i == 7 || i == 8);
     const V c = cu[odd ? oppq(i) : i];
     const V poly = p_fma(c, p_fma(k45, c, odd ? m3 : p3), nusq);
-    feq[i] = p_mul(splat<C>(wq<C>(i)), p_fma(r, poly, base));
+    if constexpr (SHIFT) {
+      feq[i] = p_mul(splat<C>(wq<C>(i)), p_fma(r, poly, base));
+    } else {
+      const V a = i <= 4 ? a1 : a5;
+      feq[i] = p_fma(a, poly, a);
+    }
   }
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
@@ -667,16 +703,20 @@ __device__ __forceinline__ void collide_thermal(const KParams<C>& kp, const C g[
   const C base = SHIFT ? dT : T;
   const V vn = splat<C>(nusq), vT = splat<C>(T), vb = splat<C>(base), k45 = splat<C>(C(4.5));
   const V pm3 = v2<C>(C(3), C(-3));
-  const C g0 = s_mul(wq<C>(0), s_fma(T, nusq, base));
+  // without a shift g^eq = w_i T (1 + P_i) = A + A P_i, A = w_i T once per weight class
+  const C g0 = SHIFT ? s_mul(wq<C>(0), s_fma(T, nusq, base)) : s_fma(s_mul(wq<C>(0), T), nusq, s_mul(wq<C>(0), T));
   post[18] = RELAX ? s_fma(s_add(g0, -g[0]), kp.inv_tau_g, g[0]) : g0;
   const C cus[4] = {uHx, uHy, s_add(uHx, uHy), s_add(uHy, -uHx)};
   const int dir[4] = {1, 2, 5, 6};
+  const V t1 = splat<C>(SHIFT ? T : s_mul(wq<C>(1), T)), t5 = splat<C>(SHIFT ? T : s_mul(wq<C>(5), T));
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int i = dir[k], o = oppq(i);
     const V c = splat<C>(cus[k]);
     const V poly = p_fma(c, p_fma(k45, c, pm3), vn);
-    V q = p_mul(splat<C>(wq<C>(i)), p_fma(vT, poly, vb));
+    V q;
+    if constexpr (SHIFT) q = p_mul(splat<C>(wq<C>(i)), p_fma(vT, poly, vb));
+    else q = p_fma(i <= 4 ? t1 : t5, poly, i <= 4 ? t1 : t5);
     if constexpr (RELAX) {
       const V pop = v2<C>(g[i], g[o]);
       q = p_fma(p_sub(q, pop), splat<C>(kp.inv_tau_g), pop);
@@ -771,9 +811,7 @@ __device__ __forceinline__ NodeMoments<C> node_moments(const SMT& sm, const KPar
   m.dr2 = dr.y;
   m.r1 = SHIFT ? m.dr1 + kp.rho_bar[0] : m.dr1;
   m.r2 = SHIFT ? m.dr2 + kp.rho_bar[1] : m.dr2;
-  m.dT = C(0);
-#pragma unroll
-  for (int i = 0; i < 9; ++i) m.dT = s_acc(m.dT, g[i]);
+  m.dT = s_sum9(g);
   m.T = m.dT + (SHIFT ? kp.T_bar : C(0));
   m.jx = sm.jx[ty][tx];
   m.jy = sm.jy[ty][tx];
@@ -1043,8 +1081,8 @@ cudaError_t launch_tile_kernel(const dim3& grid, const SF<S>* in, SF<S>* out, co
 inline dim3 rows_grid(const StepCfg& c) { return dim3((unsigned)((c.nx + 127) / 128), (unsigned)c.ny, 1u); }
 
 // rho_1 of every node (nx*ny doubles; rho_w at solid nodes) with the arithmetic of the field mode:
-// phase A's packed sum of component 1's nine populations (lane x; lane y carries zeros), plus the
-// shift in shifted storage, widened to double.  The same bits as plane 0 of MODE_FIELDS, from 9 of
+// phase A's packed sum of component 1's nine populations (p_sum9, lane x; lane y carries zeros),
+// plus the shift in shifted storage, widened to double.  The same bits as plane 0 of MODE_FIELDS, from 9 of
 // the 27 planes.
 template <class S, bool SHIFT>
 __global__ void lb_rho1_kernel(const SF<S>* __restrict__ buf, double* __restrict__ out, const KParams<SC<S>> kp) {
@@ -1059,9 +1097,10 @@ __global__ void lb_rho1_kernel(const SF<S>* __restrict__ buf, double* __restrict
     return;
   }
   const SF<S>* src = buf + (gy * kp.pitch + gx);
-  V2<C> d = splat<C>(C(0));
+  V2<C> u[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) d = p_acc(d, v2<C>(C(ld_pop<false>(src + i * kp.plane)), C(0)));
+  for (int i = 0; i < 9; ++i) u[i] = v2<C>(C(ld_pop<false>(src + i * kp.plane)), C(0));
+  const V2<C> d = p_sum9(u);
   const C r1 = SHIFT ? d.x + kp.rho_bar[0] : d.x;
   out[n] = (double)r1;
 }
