@@ -653,9 +653,10 @@ __device__ __forceinline__ void collide_fluid(const KParams<C>& kp, const C f[9]
   using V = V2<C>;
   const V r = v2<C>(r1, r2), ir = v2<C>(irl0, irl1);
   const V tau = splat<C>(kp.tau);
-  // Eq. shift: u_l = u + tau F_l / rho_l
-  const V ulx = p_fma(p_mul(tau, v2<C>(Fx[0], Fx[1])), ir, splat<C>(ux));
-  const V uly = p_fma(p_mul(tau, v2<C>(Fy[0], Fy[1])), ir, splat<C>(uy));
+  // Eq. shift: u_l = u + tau F_l / rho_l (without relaxation tau is 1 and tau F_l is F_l exactly)
+  const V fx = v2<C>(Fx[0], Fx[1]), fy = v2<C>(Fy[0], Fy[1]);
+  const V ulx = p_fma(RELAX ? p_mul(tau, fx) : fx, ir, splat<C>(ux));
+  const V uly = p_fma(RELAX ? p_mul(tau, fy) : fy, ir, splat<C>(uy));
   const V nusq = p_mul(splat<C>(C(-1.5)), p_fma(ulx, ulx, p_mul(uly, uly)));
   const V base = SHIFT ? v2<C>(dr1, dr2) : r;
   const V k45 = splat<C>(C(4.5)), p3 = splat<C>(C(3)), m3 = splat<C>(C(-3));
