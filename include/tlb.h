@@ -341,7 +341,11 @@ int lb_droplets_workspace_size(const lb_handle* h, int max_drops, size_t* bytes)
 /* Analyse the current state into d_ws (256-byte aligned, ws_bytes from lb_droplets_workspace_size
  * with the same max_drops): labels, centres, Voronoi colours, links.  *n_drops, *n_links (may be
  * NULL) receive the counts.  LB_ENOSPACE when there are more droplets than max_drops or a droplet
- * has more than 32 Voronoi neighbours.  Uses the handle's inactive buffer as staging; synchronous. */
+ * has more than 32 Voronoi neighbours.  Uses the handle's inactive buffer as staging; synchronous
+ * (one read of the workspace header at the end).  The launches are captured into a CUDA graph the
+ * first time a (d_ws, max_drops, threshold, current buffer) combination is seen and replayed after
+ * that; the handle keeps four such graphs and frees them in lb_destroy.  Not to be called while the
+ * handle's stream is being captured. */
 int lb_droplets(lb_handle* h, double threshold, int max_drops, void* d_ws, size_t ws_bytes, int* n_drops,
                 int* n_links);
 
