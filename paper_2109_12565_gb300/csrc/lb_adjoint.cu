@@ -44,7 +44,18 @@ template <class S> struct AdjTile;
 template <> struct AdjTile<double> { static constexpr int TX = 32, TY = 16, BY = 8, MINB = 1; };
 template <> struct AdjTile<float> { static constexpr int TX = 32, TY = 8, BY = 8, MINB = 3; };
 
-template <class S, class C, bool SHIFT, int TX, int TY, int BY, int MINB>
+// c v for a lattice-velocity component c in {-1, 0, 1} that is a constant once the direction loops are
+// unrolled: no product with zero is issued (IEEE arithmetic cannot drop one: 0 v is NaN for infinite
+// v and -0 for negative v), and for finite v every sum it enters keeps its value.
+template <class C> __device__ __forceinline__ C cmul(int c, C v) { return c == 0 ? C(0) : (c > 0 ? v : -v); }
+// c . v of direction i.
+template <class C> __device__ __forceinline__ C cdot(int i, C vx, C vy) {
+  return cxq(i) == 0 ? cmul(cyq(i), vy) : (cyq(i) == 0 ? cmul(cxq(i), vx) : cmul(cxq(i), vx) + cmul(cyq(i), vy));
+}
+
+// RELAX: tau or tau_g differs from 1.  Without it omega = 1, the (1 - omega) lambda terms vanish and
+// tau F / rho is F / rho, and those operations are not issued.
+template <class S, class C, bool SHIFT, bool RELAX, int TX, int TY, int BY, int MINB>
 __global__ void __launch_bounds__(TX * BY, MINB)
 lb_adj1_kernel(const S* __restrict__ fin, const S* __restrict__ lam_out, S* __restrict__ lam_in,
                S* __restrict__ lamF, const KParams<C> kp, const C cJ, const C nuc, const double mirror_coef,
@@ -56,7 +67,7 @@ lb_adj1_kernel(const S* __restrict__ fin, const S* __restrict__ lam_out, S* __re
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   tile_phase_a<S, C, SHIFT, false, TX, TY, NT, false>(fin, kp, x0, y0, sm, tid);
   const int nx = kp.nx, ny = kp.ny, pitch = kp.pitch, plane = kp.plane;
-  const C om = kp.inv_tau, omg = kp.inv_tau_g, tau = kp.tau;
+  const C om = RELAX ? kp.inv_tau : C(1), omg = RELAX ? kp.inv_tau_g : C(1), tau = RELAX ? kp.tau : C(1);
   const C Tb = SHIFT ? kp.T_bar : C(0);
   double dtd = 0.0;
 #pragma unroll 1
@@ -86,8 +97,8 @@ lb_adj1_kernel(const S* __restrict__ fin, const S* __restrict__ lam_out, S* __re
     C Fx[2], Fy[2], crx[2], cry[2], sx[2], sy[2], psl[2];
     node_force_parts<C>(sm, kp, cx, cy, r1, r2, T, Fx, Fy, crx, cry, sx, sy, psl);
     const C rho = r1 + r2;
-    const C irho = C(1) / rho;
-    const C ir[2] = {C(1) / r1, C(1) / r2};
+    C ir[2], irho;
+    three_reciprocals<C>(r1, r2, ir[0], ir[1], irho);
     const C rl2[2] = {r1, r2};
     const C ux = jx * irho, uy = jy * irho;
     const C Fxt = Fx[0] + Fx[1], Fyt = Fy[0] + Fy[1];
@@ -129,13 +140,13 @@ lb_adj1_kernel(const S* __restrict__ fin, const S* __restrict__ lam_out, S* __re
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
         const C lsv = ls[9 * l + i];
-        lin[9 * l + i] = (C(1) - om) * lsv;
+        lin[9 * l + i] = RELAX ? (C(1) - om) * lsv : C(0);
         const C lfeq = om * lsv * wq<C>(i);
-        const C cu = C(cxq(i)) * ulx + C(cyq(i)) * uly;
+        const C cu = cdot<C>(i, ulx, uly);
         lrho[l] += lfeq * (C(1) + C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
         const C g = lfeq * rl2[l];
-        lulx += g * (C(3) * C(cxq(i)) + C(9) * cu * C(cxq(i)) - C(3) * ulx);
-        luly += g * (C(3) * C(cyq(i)) + C(9) * cu * C(cyq(i)) - C(3) * uly);
+        lulx += g * (cxq(i) == 0 ? -(C(3) * ulx) : C(3 * cxq(i)) + C(9) * cu * C(cxq(i)) - C(3) * ulx);
+        luly += g * (cyq(i) == 0 ? -(C(3) * uly) : C(3 * cyq(i)) + C(9) * cu * C(cyq(i)) - C(3) * uly);
       }
       // u_l = u + tau F_l / rho_l (Eq. shift)
       lux += lulx;
@@ -150,13 +161,13 @@ lb_adj1_kernel(const S* __restrict__ fin, const S* __restrict__ lam_out, S* __re
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
         const C lsv = ls[18 + i];
-        lin[18 + i] = (C(1) - omg) * lsv;
+        lin[18 + i] = RELAX ? (C(1) - omg) * lsv : C(0);
         const C lgeq = omg * lsv * wq<C>(i);
-        const C cu = C(cxq(i)) * uHx + C(cyq(i)) * uHy;
+        const C cu = cdot<C>(i, uHx, uHy);
         lT += lgeq * (C(1) + C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
         const C g = lgeq * T;
-        luHx += g * (C(3) * C(cxq(i)) + C(9) * cu * C(cxq(i)) - C(3) * uHx);
-        luHy += g * (C(3) * C(cyq(i)) + C(9) * cu * C(cyq(i)) - C(3) * uHy);
+        luHx += g * (cxq(i) == 0 ? -(C(3) * uHx) : C(3 * cxq(i)) + C(9) * cu * C(cxq(i)) - C(3) * uHx);
+        luHy += g * (cyq(i) == 0 ? -(C(3) * uHy) : C(3 * cyq(i)) + C(9) * cu * C(cyq(i)) - C(3) * uHy);
       }
     }
     // ---- Nu seed: cJ d(<u^(H)_y T> / (kappa dT / H))/dS; the mirror-rule gradient term only moves
@@ -198,10 +209,14 @@ lb_adj1_kernel(const S* __restrict__ fin, const S* __restrict__ lam_out, S* __re
 #pragma unroll
     for (int l = 0; l < 2; ++l)
 #pragma unroll
-      for (int i = 0; i < 9; ++i)
-        lam_in[(9 * l + i) * plane + idx] = S(lin[9 * l + i] + lrho[l] + C(cxq(i)) * ljx + C(cyq(i)) * ljy);
+      for (int i = 0; i < 9; ++i) {
+        C v = RELAX ? lin[9 * l + i] + lrho[l] : lrho[l];
+        if (cxq(i) != 0) v = v + cmul(cxq(i), ljx);
+        if (cyq(i) != 0) v = v + cmul(cyq(i), ljy);
+        lam_in[(9 * l + i) * plane + idx] = S(v);
+      }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) lam_in[(18 + i) * plane + idx] = S(lin[18 + i] + lT);
+    for (int i = 0; i < 9; ++i) lam_in[(18 + i) * plane + idx] = S(RELAX ? lin[18 + i] + lT : lT);
     lamF[0 * plane + idx] = S(lFx[0]);
     lamF[1 * plane + idx] = S(lFy[0]);
     lamF[2 * plane + idx] = S(lFx[1]);
@@ -390,7 +405,9 @@ cudaError_t adj_step_impl(const StepCfg& c, const void* S_t, const void* lam_out
   using T = AdjTile<S>;
   const dim3 grid = grid_for(c.nx, c.ny, T::TX, T::TY), block(T::TX, T::BY, 1);
   const KParams<S> kp = make_kparams<S>(c);
-  auto k1 = lb_adj1_kernel<S, S, SHIFT, T::TX, T::TY, T::BY, T::MINB>;
+  auto k1r = lb_adj1_kernel<S, S, SHIFT, true, T::TX, T::TY, T::BY, T::MINB>;
+  auto k1s = lb_adj1_kernel<S, S, SHIFT, false, T::TX, T::TY, T::BY, T::MINB>;
+  auto k1 = (kp.tau_is_one && kp.tau_g_is_one) ? k1s : k1r;
   auto k2 = lb_adj2_kernel<S, S, SHIFT, T::TX, T::TY, T::BY, T::MINB>;
   constexpr size_t b1 = sizeof(TileSmem<S, T::TX, T::TY, false>), b2 = sizeof(Adj2Smem<S, T::TX, T::TY>);
   static std::atomic<unsigned long long> done{0};  // shared-memory opt-in set once per device ordinal (mod 64)
@@ -399,7 +416,8 @@ cudaError_t adj_step_impl(const StepCfg& c, const void* S_t, const void* lam_out
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(done.load() & bit)) {
-    e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1);
+    e = cudaFuncSetAttribute(k1r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k1s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2);
     if (e != cudaSuccess) return e;
     done.fetch_or(bit);
