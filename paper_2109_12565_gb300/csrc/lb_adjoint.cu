@@ -39,9 +39,13 @@ using namespace tlb;
 namespace tlb {
 
 // Tile of the reverse-step kernels and the resident CTAs per SM asked of the compiler: FP32 fits 80
-// registers without spills at 3 CTAs per SM; FP64 needs its ~240 registers (a cap spills).
+// registers without spills at 3 CTAs per SM; FP64 needs its ~240 registers (a cap spills), two
+// 128-thread CTAs per SM.  FP64 is bound by its arithmetic per node, so small tiles cost little ring
+// recompute and even out the SMs' shares: at 512 x 256, 128-node tiles leave every SM at most 7 of
+// them (896 nodes against a mean of 862), 512-node tiles up to 2 (1024).  In FP32, 16 x 8 tiles
+// measured 9% slower than 32 x 8.
 template <class S> struct AdjTile;
-template <> struct AdjTile<double> { static constexpr int TX = 32, TY = 16, BY = 8, MINB = 1; };
+template <> struct AdjTile<double> { static constexpr int TX = 16, TY = 8, BY = 8, MINB = 2; };
 template <> struct AdjTile<float> { static constexpr int TX = 32, TY = 8, BY = 8, MINB = 3; };
 
 // c v for a lattice-velocity component c in {-1, 0, 1} that is a constant once the direction loops are
