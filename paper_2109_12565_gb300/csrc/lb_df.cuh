@@ -144,7 +144,6 @@ __device__ __forceinline__ df2 p_add(df2 a, df2 b) {  // df_add per lane, packed
   const float2 h = f2_fast_two_sum(s, e, l);
   return make_df2(h, l);
 }
-__device__ __forceinline__ df2 p_acc(df2 a, df2 b) { return p_add(a, b); }
 __device__ __forceinline__ df2 p_sub(df2 a, df2 b) {
   const float2 bh = hi2(b), bl = lo2(b);
   return p_add(a, make_df2(make_float2(-bh.x, -bh.y), make_float2(-bl.x, -bl.y)));
@@ -209,7 +208,6 @@ template <> struct SSum9<df> {
 };
 
 __device__ __forceinline__ df s_add(df a, df b) { return df_add(a, b); }
-__device__ __forceinline__ df s_acc(df a, df b) { return df_add(a, b); }
 __device__ __forceinline__ df s_mul(df a, df b) { return df_mul(a, b); }
 __device__ __forceinline__ df s_fma(df a, df b, df c) { return df_fma(a, b, c); }
 

@@ -226,8 +226,7 @@ __device__ __forceinline__ double2 p_fma(double2 a, double2 b, double2 c) {
 template <class V> __device__ __forceinline__ V p_sub(V a, V b) {
   return p_fma(b, splat<decltype(a.x)>(decltype(a.x)(-1)), a);
 }
-// Accumulation of terms of one sign (the nine populations of a density, the thermal populations of a
-// node): a form with compound arithmetic may use a shorter sum there; for FP32 and FP64 it is the add.
+// The add of a running sum (p_sum9 / s_sum9 below).
 template <class V> __device__ __forceinline__ V p_acc(V a, V b) { return p_add(a, b); }
 // Scalar operations with one rounding each, never fused beyond what is written, so that every caller
 // of the functions below computes the same bits.
