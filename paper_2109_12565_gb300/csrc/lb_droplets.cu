@@ -304,9 +304,17 @@ __global__ void __launch_bounds__(kLThreads) label_local(const double* __restric
   __shared__ unsigned s_fg[kLT];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = kLThreads / 32;
   const int x0 = blockIdx.x * kLT, y0 = blockIdx.y * kLT, x = x0 + lane;
-  for (int ly = warp; ly < kLT; ly += nwarp) {
-    const int y = y0 + ly;
-    const bool fg = x < g.nx && y < g.ny && !is_solid(g, x, y) && rho1[y * g.nx + x] > threshold;
+  constexpr int kRows = kLT / (kLThreads / 32);  // rows per warp, their rho_1 loads issued together
+  double v[kRows];
+#pragma unroll
+  for (int j = 0; j < kRows; ++j) {
+    const int y = y0 + warp + j * nwarp;
+    v[j] = (x < g.nx && y < g.ny) ? rho1[y * g.nx + x] : 0.0;
+  }
+#pragma unroll
+  for (int j = 0; j < kRows; ++j) {
+    const int ly = warp + j * nwarp, y = y0 + ly;
+    const bool fg = x < g.nx && y < g.ny && !is_solid(g, x, y) && v[j] > threshold;
     const unsigned mask = __ballot_sync(0xffffffffu, fg);
     const unsigned starts = mask & ~(mask << 1);                            // first node of each run
     const int start = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));  // this lane's run (if fg)
@@ -364,33 +372,75 @@ __global__ void label_border(Geo g, int ncol, int nrow, int* lab, int* err) {
   if (!unite(lab, n, m, 1 << 26)) atomicOr(err, kErrUnion);
 }
 
+// Grid-wide node passes that give each thread kPer nodes, n = 1024 b + 256 j + t (j < kPer), issue the
+// loads of all of them before using any: one node per thread left each warp waiting on one or two
+// dependent loads at a time (at 4096 x 2048: flatten 46 -> 23 us, centre sums 58 -> 46 us).
+constexpr int kPassThreads = 256, kPer = kScanBlock / kPassThreads;
+
 // Final labels (the roots), the root bits of every 32 nodes (rmask) and per 1024-node block the number
-// of roots (the first pass of the id scan).
-__global__ void __launch_bounds__(kScanBlock) label_flatten(int N, int* lab, unsigned* __restrict__ rmask,
-                                                           int* __restrict__ bsum, int* err) {
-  __shared__ int s_warp[kScanBlock / 32];
-  const int n = blockIdx.x * kScanBlock + threadIdx.x;
-  bool root = false;
-  if (n < N) {
-    const int l = lab[n];
-    if (l >= 0) {
-      const int r = find_root(lab, n, 1 << 26);
-      if (r >= 0) {
-        lab[n] = r;  // every node of a chain resolves to the same root; concurrent writes store roots only
-        root = r == n;
+// of roots (the first pass of the id scan).  The root searches of a thread's nodes advance one parent
+// link at a time, together.
+__global__ void __launch_bounds__(kPassThreads) label_flatten(int N, int* lab, unsigned* __restrict__ rmask,
+                                                             int* __restrict__ bsum, int* err) {
+  __shared__ int s_warp[kPassThreads / 32];
+  const int base = blockIdx.x * kScanBlock + threadIdx.x;
+  int r[kPer];
+  bool fg[kPer], live[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int n = base + j * kPassThreads;
+    r[j] = n < N ? lab[n] : -1;  // the node's parent (or -1: background or outside)
+    fg[j] = r[j] >= 0;
+    live[j] = fg[j];
+  }
+  bool ok = true;
+  for (int k = 0; k < (1 << 26); ++k) {  // bounded: a parent chain is shorter than the lattice
+    int p[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) p[j] = live[j] ? lab[r[j]] : 0;
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      if (!live[j]) continue;
+      if (p[j] == r[j]) {
+        live[j] = false;  // r[j] is a root
+      } else if (p[j] < 0) {
+        live[j] = false;  // broken chain
+        r[j] = -1;
       } else {
-        atomicOr(err, kErrUnion);
+        r[j] = p[j];
+        any = true;
       }
     }
+    if (!any) break;
+    if (k + 1 == (1 << 26)) {
+#pragma unroll
+      for (int j = 0; j < kPer; ++j)
+        if (live[j]) r[j] = -1;
+    }
   }
-  const unsigned bits = __ballot_sync(0xffffffffu, root);
-  if ((threadIdx.x & 31) == 0) {
-    if (n < N) rmask[n >> 5] = bits;
-    s_warp[threadIdx.x >> 5] = __popc(bits);
+  int count = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int n = base + j * kPassThreads;
+    bool root = false;
+    if (fg[j]) {
+      if (r[j] >= 0) {
+        lab[n] = r[j];  // every node of a chain resolves to the same root; concurrent writes store roots only
+        root = r[j] == n;
+      } else {
+        ok = false;
+      }
+    }
+    const unsigned bits = __ballot_sync(0xffffffffu, root);
+    if ((threadIdx.x & 31) == 0 && n < N) rmask[n >> 5] = bits;
+    count += __popc(bits);
   }
+  if (!ok) atomicOr(err, kErrUnion);
+  if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = count;
   __syncthreads();
   if (threadIdx.x < 32) {
-    int w = s_warp[threadIdx.x];
+    int w = threadIdx.x < kPassThreads / 32 ? s_warp[threadIdx.x] : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
     if (threadIdx.x == 0) bsum[blockIdx.x] = w;
@@ -457,41 +507,51 @@ __device__ __forceinline__ int min_image_i(int d, int n) {
 // of one to the droplet's sums.  Lanes of a warp mostly see the same droplet: per distinct droplet
 // in the warp one 32-bit warp reduction and one 64-bit atomic per sum, so the sums are exact and
 // order independent.
-__global__ void centre_sums(Geo g, const int* __restrict__ lab, const unsigned* __restrict__ rmask,
-                            const int* __restrict__ woff, const Header* __restrict__ h, int* __restrict__ did,
-                            int* __restrict__ root, unsigned long long* cnt, long long* sx, long long* sy) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kPassThreads) centre_sums(Geo g, const int* __restrict__ lab,
+                                                           const unsigned* __restrict__ rmask,
+                                                           const int* __restrict__ woff,
+                                                           const Header* __restrict__ h, int* __restrict__ did,
+                                                           int* __restrict__ root, unsigned long long* cnt,
+                                                           long long* sx, long long* sy) {
   const int N = g.nx * g.ny;
-  int d = -1, l = -1;
-  if (n < N) {
-    l = lab[n];
-    if (l >= 0) d = root_id(rmask, woff, l);
-    did[n] = d;
+  const int base = blockIdx.x * kScanBlock + threadIdx.x;
+  int l[kPer], d[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int n = base + j * kPassThreads;
+    l[j] = n < N ? lab[n] : -1;
   }
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) d[j] = l[j] >= 0 ? root_id(rmask, woff, l[j]) : -1;
   const int n_drops = h->n_drops;
-  const bool mine = d >= 0 && d < n_drops;
-  if (mine && l == n) root[d] = n;
-  int dx = 0, dy = 0;
-  if (mine) {
-    const int x = n % g.nx, y = n / g.nx, rx = l % g.nx, ry = l / g.nx;
-    dx = min_image_i(x - rx, g.nx);
-    dy = g.periodic_y ? min_image_i(y - ry, g.ny) : (y - ry);
-  }
-  const unsigned active = __ballot_sync(0xffffffffu, mine);
-  if (!mine) return;
-  unsigned rest = active;
-  while (rest) {  // one iteration per distinct droplet among the active lanes (at most 32)
-    const int dl = __shfl_sync(active, d, __ffs(rest) - 1);
-    const bool in_group = d == dl;
-    const unsigned group = __ballot_sync(active, in_group);
-    const int gx = __reduce_add_sync(active, in_group ? dx : 0);
-    const int gy = __reduce_add_sync(active, in_group ? dy : 0);
-    if ((int)(threadIdx.x & 31) == __ffs(group) - 1) {
-      atomicAdd(cnt + dl, (unsigned long long)__popc(group));
-      atomicAdd(reinterpret_cast<unsigned long long*>(sx + dl), (unsigned long long)(long long)gx);
-      atomicAdd(reinterpret_cast<unsigned long long*>(sy + dl), (unsigned long long)(long long)gy);
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int n = base + j * kPassThreads;
+    if (n < N) did[n] = d[j];
+    const bool mine = d[j] >= 0 && d[j] < n_drops;
+    if (mine && l[j] == n) root[d[j]] = n;
+    int dx = 0, dy = 0;
+    if (mine) {
+      const int x = n % g.nx, y = n / g.nx, rx = l[j] % g.nx, ry = l[j] / g.nx;
+      dx = min_image_i(x - rx, g.nx);
+      dy = g.periodic_y ? min_image_i(y - ry, g.ny) : (y - ry);
     }
-    rest &= ~group;
+    const unsigned active = __ballot_sync(0xffffffffu, mine);
+    if (!mine) continue;
+    unsigned rest = active;
+    while (rest) {  // one iteration per distinct droplet among the active lanes (at most 32)
+      const int dl = __shfl_sync(active, d[j], __ffs(rest) - 1);
+      const bool in_group = d[j] == dl;
+      const unsigned group = __ballot_sync(active, in_group);
+      const int gx = __reduce_add_sync(active, in_group ? dx : 0);
+      const int gy = __reduce_add_sync(active, in_group ? dy : 0);
+      if ((int)(threadIdx.x & 31) == __ffs(group) - 1) {
+        atomicAdd(cnt + dl, (unsigned long long)__popc(group));
+        atomicAdd(reinterpret_cast<unsigned long long*>(sx + dl), (unsigned long long)(long long)gx);
+        atomicAdd(reinterpret_cast<unsigned long long*>(sy + dl), (unsigned long long)(long long)gy);
+      }
+      rest &= ~group;
+    }
   }
 }
 
@@ -824,13 +884,15 @@ __device__ __forceinline__ void adj_insert(int* adj, int* deg, int a, int b, int
   atomicOr(err, kErrDegree);
 }
 
+// Links (D6) of the 2 x 2 window whose lower-left corner is node n (corners in cyclic order 00, 10, 11,
+// 01), one window per thread: few windows hold three or four colours, and each of those runs its
+// inserts one after another (four windows per thread measured 1.5-2x slower).
 __global__ void voronoi_links(Geo g, const int* __restrict__ col, int* adj, int* deg, int* err) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.nx * g.ny) return;
   const int x = n % g.nx, y = n / g.nx;
   if (!g.periodic_y && y == g.ny - 1) return;
   const int x1 = x + 1 == g.nx ? 0 : x + 1, y1 = y + 1 == g.ny ? 0 : y + 1;
-  // corners in cyclic order: 00, 10, 11, 01
   const int c[4] = {col[y * g.nx + x], col[y * g.nx + x1], col[y1 * g.nx + x1], col[y1 * g.nx + x]};
   if (c[0] < 0 || c[1] < 0 || c[2] < 0 || c[3] < 0) return;
   if (c[0] == c[1] && c[1] == c[2] && c[2] == c[3]) return;
@@ -1137,12 +1199,12 @@ cudaError_t enqueue_analysis(const lb_handle* h, const DView& v, const DLayout& 
   const int ncol = (h->p.nx + kLT - 1) / kLT, nrow = (h->p.ny + kLT - 1) / kLT;
   label_local<<<dim3((unsigned)ncol, (unsigned)nrow), kLThreads, 0, s>>>(stage, threshold, g, v.lab, err);
   label_border<<<nb((long long)h->p.ny * ncol + (long long)h->p.nx * nrow, T), T, 0, s>>>(g, ncol, nrow, v.lab, err);
-  label_flatten<<<L.nblk, kScanBlock, 0, s>>>(N, v.lab, v.rmask, v.blk, err);
+  label_flatten<<<L.nblk, kPassThreads, 0, s>>>(N, v.lab, v.rmask, v.blk, err);
   label_count<<<1, kScanBlock, 0, s>>>(v.blk, L.nblk, v.hdr, max_drops);
   const int n_words = (N + 31) / 32;
   warp_offsets<<<nb(n_words, T), T, 0, s>>>(n_words, v.rmask, v.blk, v.woff);
   // centres (D4) and the cell grid of the centres
-  centre_sums<<<nb(N, T), T, 0, s>>>(g, v.lab, v.rmask, v.woff, v.hdr, v.did, v.root, v.cnt, v.sx, v.sy);
+  centre_sums<<<L.nblk, kPassThreads, 0, s>>>(g, v.lab, v.rmask, v.woff, v.hdr, v.did, v.root, v.cnt, v.sx, v.sy);
   centre_final<<<per_drop, T, 0, s>>>(g, v.hdr, v.root, v.cnt, v.sx, v.sy, v.cx, v.cy, L.ncx, L.ncy, v.ccount, v.lcount,
                                       v.crec_id);
   cell_fill<<<1, kScanBlock, 0, s>>>(v.hdr, L.ncell, v.ccount, v.cstart, v.lcount, v.cfill, v.citems, v.crec_id,
