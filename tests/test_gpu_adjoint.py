@@ -54,6 +54,26 @@ def test_adjoint_step_matches_oracle(cJ, with_lam):
     assert abs(got_d - want_d) <= 1e-10 * max(abs(want_d), 1e-12)
 
 
+@pytest.mark.parametrize("tau,tau_g", [(0.8, 1.0), (0.75, 0.9)])
+def test_adjoint_step_with_relaxation_matches_oracle(tau, tau_g):
+    """tau or tau_g away from 1 selects the reverse-step kernel that carries the relaxation terms."""
+    w, mask = _small()
+    params = dict(w.params, tau=tau, tau_g=tau_g)
+    o = O.Oracle(params, w.rho1, w.rho2, w.T0, mask=mask)
+    o.step(20)
+    g = lb.Lattice(params, w.rho1, w.rho2, w.T0, mask=mask)
+    g.set_state(o.state)
+    solid = o.solid().astype(bool)
+    lam_next = I.uniform(78, o.state.size).reshape(o.state.shape) - 0.5
+    lam_next[:, solid] = 0.0
+    want, want_d = O.adjoint_step(params, o.state, lam_next, 0.37, mask=mask)
+    lam_dev, got_d = g.adjoint_step(g.to_device_vector(lam_next), 0.37)
+    got = g.from_device_vector(lam_dev)
+    scale = np.abs(want).max()
+    assert np.abs(got - want).max() <= 1e-10 * scale, np.abs(got - want).max() / scale
+    assert abs(got_d - want_d) <= 1e-10 * max(abs(want_d), 1e-12)
+
+
 def test_adjoint_gradient_matches_oracle_gradient():
     w, mask = _small(nx=40, ny=24)
     N = 60
