@@ -597,18 +597,20 @@ __global__ void centre_final(Geo g, const Header* __restrict__ h, const int* __r
   }
 }
 
-// One block: cell starts (exclusive scan of the counts), the cell lists of droplet ids and the centre
-// records in the same order.
-__global__ void __launch_bounds__(kScanBlock) cell_fill(const Header* __restrict__ h, int ncell,
-                                                       const int* __restrict__ ccount, int* __restrict__ cstart,
-                                                       const int* __restrict__ dcell, int* cfill,
-                                                       int* __restrict__ citems, const CRec* __restrict__ rec_id,
-                                                       CRec* __restrict__ rec) {
+// One block: cell starts (exclusive scan of the counts).
+__global__ void __launch_bounds__(kScanBlock) cell_scan(int ncell, const int* __restrict__ ccount,
+                                                       int* __restrict__ cstart) {
   __shared__ int s_warp[kScanBlock / 32];
   block_scan_loop(ccount, cstart, ncell, s_warp);
-  __syncthreads();  // the starts written by the other threads of this block are visible after the barrier
+}
+
+// Per droplet (grid-stride over the count in the header): its slot in its cell's list of droplet ids,
+// and its centre record at the same slot.
+__global__ void cell_fill(const Header* __restrict__ h, const int* __restrict__ cstart,
+                          const int* __restrict__ dcell, int* cfill, int* __restrict__ citems,
+                          const CRec* __restrict__ rec_id, CRec* __restrict__ rec) {
   const int n_drops = h->n_drops;
-  for (int d = threadIdx.x; d < n_drops; d += kScanBlock) {
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n_drops; d += gridDim.x * blockDim.x) {
     const int c = dcell[d];
     const int at = cstart[c] + atomicAdd(cfill + c, 1);
     citems[at] = d;
@@ -1207,8 +1209,8 @@ cudaError_t enqueue_analysis(const lb_handle* h, const DView& v, const DLayout& 
   centre_sums<<<L.nblk, kPassThreads, 0, s>>>(g, v.lab, v.rmask, v.woff, v.hdr, v.did, v.root, v.cnt, v.sx, v.sy);
   centre_final<<<per_drop, T, 0, s>>>(g, v.hdr, v.root, v.cnt, v.sx, v.sy, v.cx, v.cy, L.ncx, L.ncy, v.ccount, v.lcount,
                                       v.crec_id);
-  cell_fill<<<1, kScanBlock, 0, s>>>(v.hdr, L.ncell, v.ccount, v.cstart, v.lcount, v.cfill, v.citems, v.crec_id,
-                                     v.crec);
+  cell_scan<<<1, kScanBlock, 0, s>>>(L.ncell, v.ccount, v.cstart);
+  cell_fill<<<per_drop, T, 0, s>>>(v.hdr, v.cstart, v.lcount, v.cfill, v.citems, v.crec_id, v.crec);
   // colours (D5) and links (D6)
   const Grid G = grid_of(v, L, h->p);
   voronoi_tiled<<<dim3((unsigned)((h->p.nx + kVTX - 1) / kVTX), (unsigned)((h->p.ny + kVTY - 1) / kVTY)),
