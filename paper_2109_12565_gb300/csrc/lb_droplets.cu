@@ -679,18 +679,6 @@ __device__ int nearest_centre(const Geo& g, const Grid& G, double x, double y, d
 
 // ---------------------------------------------------------------- colours and links (D5, D6)
 
-// Colours of one 32 x 8 tile per CTA (one node per thread).
-//
-// Staging: the records of every cell within 2 cells of the cells the tile's nodes lie in (x periodic;
-// y periodic or clipped) go to shared memory.  Any centre not staged lies at least 2 cells from a
-// node's cell, so farther than 1 cell edge (a conservative bound): a node whose best staged distance
-// is below one cell edge has its exact answer; otherwise (and when the staging list overflows) it runs
-// the full ring search.  The staged list is then cut to the centres that can be nearest to a node of
-// the tile: the centre nearest to the tile's middle bounds every node's nearest distance by U (its
-// distance + the half-diagonal), and a centre farther than U from the tile box is nobody's nearest
-// (nor tied).  FP32 with margins far above its rounding (1e-4 relative, 1e-2 absolute) keeps U an
-// upper bound.
-//
 // Nearest centre: distances screened in FP32.  The node's integer offset from a centre's integer part
 // is exact; the minimum image is decided on the offset less the fraction's high part (as the oracle
 // decides it on its offset; a decision that differs within an ulp of +-n/2 changes |dx| by an ulp),
@@ -701,53 +689,73 @@ __device__ int nearest_centre(const Geo& g, const Grid& G, double x, double y, d
 // node within that margin of a Voronoi edge) the candidates inside the margin are compared in FP64
 // with the oracle's arithmetic and tie rule.  FP64 runs at 1/64 of the FP32 rate on this part, so
 // the screen decides almost every node without it.
-constexpr int kVTX = 32, kVTY = 8, kVThreads = kVTX * kVTY, kVList = 512;
+//
+// Staging: a node's centre is looked for among the records of the cells within 2 cells of the node's
+// cell (x periodic; y periodic or clipped).  Any centre not staged lies at least 2 cells from the
+// node's cell, so farther than 1 cell edge (a conservative bound): a node whose best staged distance
+// is below one cell edge has its exact answer; otherwise (and when the staging list overflows) it
+// runs the full ring search.  The staged list is first cut to the centres that can be nearest to a
+// node of the group: the centre nearest to the group's middle bounds every node's nearest distance
+// by U (its distance + the half-extent of the group), and a centre farther than U from the group's
+// box is nobody's nearest (nor tied).  FP32 with margins far above its rounding (1e-4 relative, 1e-2
+// absolute) keeps U an upper bound.
+constexpr int kVTX = 32, kVTY = 8, kVThreads = kVTX * kVTY;
 
-__global__ void __launch_bounds__(kVThreads) voronoi_tiled(Geo g, Grid G, const CRec* __restrict__ rec,
-                                                           const Header* __restrict__ h, int* __restrict__ col) {
-  __shared__ CRec s_r[kVList];
-  __shared__ float s_red[kVThreads / 32];
-  __shared__ int s_n, s_m, s_range[4];
+// Colours with one warp per row of 32 nodes (8 rows a CTA) and no CTA barrier: each warp stages the
+// records of the cells within 2 cells of its row's cells (lane = cell, a warp scan places them), cuts
+// them to the centres within U of its row, and screens them for its 32 nodes; only __syncwarp orders
+// the steps.  The eight warps of a CTA stage overlapping cells (the repeats hit L1).  A 32 x 8 tile
+// staged once by the CTA, with CTA barriers between staging, cut and screen, measured 2% slower.
+constexpr int kWList = 64;  // staged records per warp; more falls back to the ring search
+
+__global__ void __launch_bounds__(kVThreads) voronoi_rows(Geo g, Grid G, const CRec* __restrict__ rec,
+                                                          const Header* __restrict__ h, int* __restrict__ col) {
+  __shared__ CRec s_r[kVTY][kWList];
+  __shared__ int s_k[kVTY][kWList];  // indices of the kept records
+  const int lane = threadIdx.x, wy = threadIdx.y;
   const int n_drops = h->n_drops;
-  const int x0 = blockIdx.x * kVTX, y0 = blockIdx.y * kVTY;
-  const int tid = threadIdx.y * kVTX + threadIdx.x;
-  const int w = min(kVTX, g.nx - x0), ht = min(kVTY, g.ny - y0);
-  if (tid == 0) {
-    // cell range of the tile's nodes, widened by 2 cells: floor(x * ncx / nx) in exact integer
-    // arithmetic (the same cell as the FP64 quotient, whose rounding cannot cross an integer)
-    s_range[0] = (int)((long long)x0 * G.ncx / g.nx) - 2;
-    s_range[1] = (int)((long long)(x0 + w - 1) * G.ncx / g.nx) + 2;
-    s_range[2] = (int)((long long)y0 * G.ncy / g.ny) - 2;
-    s_range[3] = (int)((long long)(y0 + ht - 1) * G.ncy / g.ny) + 2;
-    s_n = 0;
-    s_m = 0;
-  }
-  __syncthreads();
-  const int cx0 = s_range[0], cy0 = s_range[2];
-  const int wx = s_range[1] - cx0 + 1, wy = s_range[3] - cy0 + 1;
-  bool overflow = false;
-  for (int c = tid; c < wx * wy && n_drops > 0; c += kVThreads) {
-    const int jy = cy0 + c / wx, jx = cx0 + c % wx;
-    int cyi = jy;
-    if (g.periodic_y) cyi = ((jy % G.ncy) + G.ncy) % G.ncy;
-    else if (jy < 0 || jy >= G.ncy) continue;
-    const int cxi = ((jx % G.ncx) + G.ncx) % G.ncx;
-    const int cell = cyi * G.ncx + cxi;
-    const int s = G.cstart[cell], n = G.ccount[cell];
-    if (n == 0) continue;
-    const int at = atomicAdd(&s_n, n);
-    if (at + n > kVList) {
-      overflow = true;
-      continue;
+  const int x0 = blockIdx.x * kVTX, y = blockIdx.y * kVTY + wy;
+  if (y >= g.ny) return;  // a whole warp: no later warp-wide operation misses a lane
+  const int w = min(kVTX, g.nx - x0);
+  CRec* const sr = s_r[wy];
+  int* const sk = s_k[wy];
+  // the warp's cells: x range widened by 2 cells (a window wider than the grid takes each cell once),
+  // rows cy - 2 .. cy + 2 (periodic, or clipped)
+  const int cxa = (int)((long long)x0 * G.ncx / g.nx) - 2, cxb = (int)((long long)(x0 + w - 1) * G.ncx / g.nx) + 2;
+  const int cyc = (int)((long long)y * G.ncy / g.ny);
+  const int span = min(cxb - cxa + 1, G.ncx);
+  const int rows = g.periodic_y ? min(5, G.ncy) : 5;
+  const int ry0 = g.periodic_y && rows < 5 ? 0 : cyc - 2;
+  const int ncell = span * rows;
+  int start = 0, cnt = 0;
+  if (lane < ncell && n_drops > 0) {
+    const int r = lane / span, cxi = ((cxa + lane - r * span) % G.ncx + G.ncx) % G.ncx;
+    int cyi = ry0 + r;
+    bool ok = true;
+    if (g.periodic_y) cyi = (cyi % G.ncy + G.ncy) % G.ncy;
+    else ok = cyi >= 0 && cyi < G.ncy;
+    if (ok) {
+      const int cell = cyi * G.ncx + cxi;
+      start = G.cstart[cell];
+      cnt = G.ccount[cell];
     }
-    for (int k = 0; k < n; ++k) s_r[at + k] = rec[s + k];
   }
-  const bool staged = !__syncthreads_or(overflow ? 1 : 0) && n_drops > 0;
-  int m = s_n;
-  if (staged && m > 0) {
-    const float hw = 0.5f * (float)(w - 1), hh = 0.5f * (float)(ht - 1);
-    const float tcx = (float)x0 + hw, tcy = (float)y0 + hh;
-    auto offset = [&](const CRec& r, float& ax, float& ay) {  // |centre - tile middle|, minimum image
+  int off = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, off, o);
+    if (lane >= o) off += t;
+  }
+  const int total = __shfl_sync(0xffffffffu, off, 31);
+  off -= cnt;
+  const bool staged = n_drops > 0 && ncell <= 32 && total <= kWList;
+  int m = 0;
+  if (staged && total > 0) {
+    for (int k = 0; k < cnt; ++k) sr[off + k] = rec[start + k];
+    __syncwarp();
+    const float hw = 0.5f * (float)(w - 1);
+    const float tcx = (float)x0 + hw, tcy = (float)y;
+    auto offset = [&](const CRec& r, float& ax, float& ay) {  // |centre - row middle|, minimum image
       float dx = ((float)r.i.x - tcx) + r.f.x, dy = ((float)r.i.y - tcy) + r.f.z;
       if (dx > 0.5f * g.nx) dx -= (float)g.nx;
       else if (dx < -0.5f * g.nx) dx += (float)g.nx;
@@ -758,44 +766,30 @@ __global__ void __launch_bounds__(kVThreads) voronoi_tiled(Geo g, Grid G, const 
       ax = fabsf(dx);
       ay = fabsf(dy);
     };
-    float dmin = 3.0e38f;
-    for (int k = tid; k < m; k += kVThreads) {
-      float ax, ay;
-      offset(s_r[k], ax, ay);
-      dmin = fminf(dmin, ax * ax + ay * ay);
+    float a0x = 3.0e38f, a0y = 0.0f, a1x = 3.0e38f, a1y = 0.0f, dmin = 3.0e38f;
+    if (lane < total) {
+      offset(sr[lane], a0x, a0y);
+      dmin = a0x * a0x + a0y * a0y;
+    }
+    if (lane + 32 < total) {
+      offset(sr[lane + 32], a1x, a1y);
+      dmin = fminf(dmin, a1x * a1x + a1y * a1y);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
-    if ((tid & 31) == 0) s_red[tid >> 5] = dmin;
-    __syncthreads();
-    dmin = s_red[0];
-#pragma unroll
-    for (int i = 1; i < kVThreads / 32; ++i) dmin = fminf(dmin, s_red[i]);
-    const float U = (sqrtf(dmin) + sqrtf(hw * hw + hh * hh)) * 1.0001f + 0.01f;
-    constexpr int PER = kVList / kVThreads;  // each thread holds its kept records across the barrier
-    CRec kr[PER];
-    bool kk[PER];
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-      const int k = tid + j * kVThreads;
-      kk[j] = false;
-      if (k < m) {
-        kr[j] = s_r[k];
-        float ax, ay;
-        offset(kr[j], ax, ay);
-        const float ex = fmaxf(ax - hw, 0.0f), ey = fmaxf(ay - hh, 0.0f);
-        kk[j] = ex * ex + ey * ey <= U * U;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < PER; ++j)
-      if (kk[j]) s_r[atomicAdd(&s_m, 1)] = kr[j];
-    __syncthreads();
-    m = s_m;
+    const float U = (sqrtf(dmin) + hw) * 1.0001f + 0.01f;
+    const float e0 = fmaxf(a0x - hw, 0.0f), e1 = fmaxf(a1x - hw, 0.0f);
+    const bool k0 = lane < total && e0 * e0 + a0y * a0y <= U * U;
+    const bool k1 = lane + 32 < total && e1 * e1 + a1y * a1y <= U * U;
+    const unsigned b0 = __ballot_sync(0xffffffffu, k0), b1 = __ballot_sync(0xffffffffu, k1);
+    const unsigned below = (1u << lane) - 1u;
+    if (k0) sk[__popc(b0 & below)] = lane;
+    if (k1) sk[__popc(b0) + __popc(b1 & below)] = lane + 32;
+    m = __popc(b0) + __popc(b1);
+    __syncwarp();
   }
-  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-  if (threadIdx.x >= w || threadIdx.y >= ht) return;
+  const int x = x0 + lane;
+  if (lane >= w) return;
   const int n = y * g.nx + x;
   if (is_solid(g, x, y) || n_drops == 0) {
     col[n] = -1;
@@ -818,11 +812,11 @@ __global__ void __launch_bounds__(kVThreads) voronoi_tiled(Geo g, Grid G, const 
   };
   int best_id = -1;
   bool settled = false;
-  if (staged) {
-    float b1 = 3.0e38f, b2 = 3.0e38f;  // best and second-best screened distances
+  if (staged && m > 0) {
+    float b1 = 3.0e38f, b2 = 3.0e38f;
     int k1 = -1;
     for (int k = 0; k < m; ++k) {
-      const float d2 = screen(s_r[k]);
+      const float d2 = screen(sr[sk[k]]);
       if (d2 < b1) {
         b2 = b1;
         b1 = d2;
@@ -832,27 +826,27 @@ __global__ void __launch_bounds__(kVThreads) voronoi_tiled(Geo g, Grid G, const 
       }
     }
     const float keep = b1 * 1.00001f + 1e-3f;
-    if (k1 >= 0 && b2 > keep) {
-      best_id = s_r[k1].id;
+    if (b2 > keep) {
+      best_id = sr[sk[k1]].id;
       settled = keep < G.cw2_f;
-    } else if (k1 >= 0) {
+    } else {
       const double px = (double)x, py = (double)y, hx = 0.5 * g.nx, hy = 0.5 * g.ny;
       double best = 0.0;
-      for (int k = 0; k < m; ++k) {
-        if (screen(s_r[k]) > keep) continue;
-        double dx = __dsub_rn(px, s_r[k].x);
+      for (int kk = 0; kk < m; ++kk) {
+        const CRec& r = sr[sk[kk]];
+        if (screen(r) > keep) continue;
+        double dx = __dsub_rn(px, r.x);
         if (dx > hx) dx = __dsub_rn(dx, (double)g.nx);
         else if (dx < -hx) dx = __dadd_rn(dx, (double)g.nx);
-        double dy = __dsub_rn(py, s_r[k].y);
+        double dy = __dsub_rn(py, r.y);
         if (g.periodic_y) {
           if (dy > hy) dy = __dsub_rn(dy, (double)g.ny);
           else if (dy < -hy) dy = __dadd_rn(dy, (double)g.ny);
         }
         const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-        const int d = s_r[k].id;
-        if (best_id < 0 || d2 < best || (d2 == best && d < best_id)) {
+        if (best_id < 0 || d2 < best || (d2 == best && r.id < best_id)) {
           best = d2;
-          best_id = d;
+          best_id = r.id;
         }
       }
       settled = best_id >= 0 && best < G.cw_min * G.cw_min;
@@ -1213,8 +1207,8 @@ cudaError_t enqueue_analysis(const lb_handle* h, const DView& v, const DLayout& 
   cell_fill<<<per_drop, T, 0, s>>>(v.hdr, v.cstart, v.lcount, v.cfill, v.citems, v.crec_id, v.crec);
   // colours (D5) and links (D6)
   const Grid G = grid_of(v, L, h->p);
-  voronoi_tiled<<<dim3((unsigned)((h->p.nx + kVTX - 1) / kVTX), (unsigned)((h->p.ny + kVTY - 1) / kVTY)),
-                  dim3(kVTX, kVTY), 0, s>>>(g, G, v.crec, v.hdr, v.col);
+  voronoi_rows<<<dim3((unsigned)((h->p.nx + kVTX - 1) / kVTX), (unsigned)((h->p.ny + kVTY - 1) / kVTY)),
+                 dim3(kVTX, kVTY), 0, s>>>(g, G, v.crec, v.hdr, v.col);
   voronoi_links<<<nb(N, T), T, 0, s>>>(g, v.col, v.adj, v.deg, err);
   adj_sort<<<per_drop_warps, T, 0, s>>>(v.hdr, v.adj, v.deg, v.lcount);
   links_count<<<1, kScanBlock, 0, s>>>(v.hdr, v.lcount, v.loff);
