@@ -47,7 +47,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # FP64 (non-tensor) peak from the unit counts and the clock: 152 SMs x 2 FP64 FMA per clock per SM
 # x 2 flops per FMA x the maximum SM clock (MEASURED_PEAKS.json sm_max_mhz, else 2070 MHz).
 FP64_SMS, FP64_FMA_PER_CLK_PER_SM = 152, 2
-DETAIL_DEFAULT = os.path.join("gpurun_out", "bench_detail.json")
+DETAIL_DEFAULT = os.path.join("_build", "bench_detail.json")  # git-ignored
 
 
 def _peaks():
