@@ -258,7 +258,7 @@ def test_fp32_shifted_state_roundtrip():
 
 
 @pytest.mark.parametrize("precision,steps,tol", [(lb.LB_FP64, 12, 1e-12), (lb.LB_FP32_SHIFTED, 12, 1e-4),
-                                                 (lb.LB_FP32_FP16T, 12, FP16T_T_TOL)])
+                                                 (lb.LB_FP32_FP16T, 12, FP16T_T_TOL), (lb.LB_DF64, 12, 1e-12)])
 def test_full_size_1024x512_against_oracle(precision, steps, tol):
     """The 1024 x 512 concentrated emulsion in the launch configuration the benchmark times, checked
     against the oracle on every node (the OpenMP oracle finishes this in seconds)."""
@@ -272,7 +272,7 @@ def test_full_size_1024x512_against_oracle(precision, steps, tol):
     g.step(steps)
     o.step(steps)
     fg, fo = g.fields(), o.fields()
-    if precision == lb.LB_FP64:
+    if precision in (lb.LB_FP64, lb.LB_DF64):
         d = _max_field_diff(fg, fo)
         assert max(d.values()) <= tol, d
         assert np.abs(g.get_state() - o.state).max() <= tol
