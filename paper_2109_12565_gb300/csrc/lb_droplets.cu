@@ -625,7 +625,8 @@ struct Grid {
   const int *cstart, *ccount, *citems;
   int ncx, ncy;
   double cw_min;  // smaller cell edge
-  float cw2_f;    // cw_min^2 rounded down to FP32
+  double cw2_d;   // (2 cw_min)^2 (1 - 1e-9): a staged nearest distance below it is exact
+  float cw2_f;    // cw2_d rounded down to FP32
 };
 
 // Nearest centre to (x, y): rings of cells around the point's cell until no unvisited cell can hold a
@@ -691,10 +692,11 @@ __device__ int nearest_centre(const Geo& g, const Grid& G, double x, double y, d
 // the screen decides almost every node without it.
 //
 // Staging: a node's centre is looked for among the records of the cells within 2 cells of the node's
-// cell (x periodic; y periodic or clipped).  Any centre not staged lies at least 2 cells from the
-// node's cell, so farther than 1 cell edge (a conservative bound): a node whose best staged distance
-// is below one cell edge has its exact answer; otherwise (and when the staging list overflows) it
-// runs the full ring search.  The staged list is first cut to the centres that can be nearest to a
+// cell (x periodic; y periodic or clipped).  Any centre not staged sits in a cell 3 or more cells from
+// the node's cell in x or y, so with two whole cells in between it lies more than 2 cell edges away
+// (less about 1e-12 where the FP64 cell index of a centre on a cell boundary rounds up; the 1e-9
+// factor of cw2_d covers it): a node whose best staged distance is below 2 cell edges has its exact
+// answer; otherwise (and when the staging list overflows) it runs the full ring search.  The staged list is first cut to the centres that can be nearest to a
 // node of the group: the centre nearest to the group's middle bounds every node's nearest distance
 // by U (its distance + the half-extent of the group), and a centre farther than U from the group's
 // box is nobody's nearest (nor tied).  FP32 with margins far above its rounding (1e-4 relative, 1e-2
@@ -849,7 +851,7 @@ __global__ void __launch_bounds__(kVThreads) voronoi_rows(Geo g, Grid G, const C
           best_id = r.id;
         }
       }
-      settled = best_id >= 0 && best < G.cw_min * G.cw_min;
+      settled = best_id >= 0 && best < G.cw2_d;
     }
   }
   if (!settled) best_id = nearest_centre(g, G, (double)x, (double)y, nullptr);
@@ -1156,8 +1158,9 @@ Grid grid_of(const DView& v, const DLayout& L, const lb_params& p) {
   G.ncy = L.ncy;
   const double wx = (double)p.nx / L.ncx, wy = (double)p.ny / L.ncy;
   G.cw_min = wx < wy ? wx : wy;
-  G.cw2_f = (float)(G.cw_min * G.cw_min);
-  if ((double)G.cw2_f > G.cw_min * G.cw_min) G.cw2_f = std::nextafter(G.cw2_f, 0.0f);
+  G.cw2_d = 4.0 * G.cw_min * G.cw_min * (1.0 - 1e-9);
+  G.cw2_f = (float)G.cw2_d;
+  if ((double)G.cw2_f > G.cw2_d) G.cw2_f = std::nextafter(G.cw2_f, 0.0f);
   return G;
 }
 
