@@ -111,7 +111,8 @@ typedef struct lb_obs {
 typedef struct lb_handle lb_handle;
 
 /* Bytes of device workspace lb_init needs for these parameters; has_mask != 0 when an obstacle
- * mask will be passed.  Returns LB_EINVAL on invalid parameters. */
+ * mask will be passed.  Returns LB_EINVAL on invalid parameters, among them lattices beyond the size
+ * limits: nx * ny < 2^31, 27 * pitch * ny < 2^31 population slots per buffer, ny <= 65535. */
 int lb_workspace_size(const lb_params* p, int has_mask, size_t* bytes);
 
 /* Create a lattice on the current CUDA device.  rho1, rho2, T0: host arrays of nx*ny doubles (x

@@ -34,6 +34,8 @@ inline const char* check_params(const lb_params* p) {
   if (!p) return "params is NULL";
   if (p->nx < 1 || p->ny < 1) return "nx and ny must be >= 1";
   if ((long long)p->nx * p->ny > (1LL << 31) - 1) return "nx * ny must fit in 31 bits";
+  // the row-wise kernels (init, field read-back, rho_1) launch one block row per lattice row
+  if (p->ny > 65535) return "ny must be <= 65535";
   if (!p->periodic_y && p->ny < 3) return "walls (periodic_y = 0) need ny >= 3";
   if (p->precision != LB_FP64 && p->precision != LB_FP32_SHIFTED && p->precision != LB_FP32_FP16T &&
       p->precision != LB_DF64)

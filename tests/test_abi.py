@@ -60,7 +60,8 @@ def test_workspace_size_layout():
 
 
 @pytest.mark.parametrize("bad", [dict(tau=0.5), dict(tau_g=0.4), dict(rho0=0.0), dict(nx=0), dict(ny=2),
-                                 dict(precision=7), dict(G12=math.inf), dict(rho_wall=(0.0, 0.5))])
+                                 dict(precision=7), dict(G12=math.inf), dict(rho_wall=(0.0, 0.5)),
+                                 dict(nx=32, ny=65536), dict(nx=16384, ny=4864)])
 def test_invalid_parameters_rejected(bad):
     p = dict(I.emulsion_small().params)
     p.update(bad)
