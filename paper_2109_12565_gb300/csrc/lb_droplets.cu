@@ -886,9 +886,8 @@ __device__ __forceinline__ void adj_insert(int* adj, int* deg, int a, int b, int
 // 01), one window per thread: few windows hold three or four colours, and each of those runs its
 // inserts one after another (four windows per thread measured 1.5-2x slower).
 __global__ void voronoi_links(Geo g, const int* __restrict__ col, int* adj, int* deg, int* err) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= g.nx * g.ny) return;
-  const int x = n % g.nx, y = n / g.nx;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;  // one block row per lattice row
+  if (x >= g.nx) return;
   if (!g.periodic_y && y == g.ny - 1) return;
   const int x1 = x + 1 == g.nx ? 0 : x + 1, y1 = y + 1 == g.ny ? 0 : y + 1;
   const int c[4] = {col[y * g.nx + x], col[y * g.nx + x1], col[y1 * g.nx + x1], col[y1 * g.nx + x]};
@@ -1212,7 +1211,7 @@ cudaError_t enqueue_analysis(const lb_handle* h, const DView& v, const DLayout& 
   const Grid G = grid_of(v, L, h->p);
   voronoi_rows<<<dim3((unsigned)((h->p.nx + kVTX - 1) / kVTX), (unsigned)((h->p.ny + kVTY - 1) / kVTY)),
                  dim3(kVTX, kVTY), 0, s>>>(g, G, v.crec, v.hdr, v.col);
-  voronoi_links<<<nb(N, T), T, 0, s>>>(g, v.col, v.adj, v.deg, err);
+  voronoi_links<<<dim3(nb(h->p.nx, T), (unsigned)h->p.ny), T, 0, s>>>(g, v.col, v.adj, v.deg, err);
   adj_sort<<<per_drop_warps, T, 0, s>>>(v.hdr, v.adj, v.deg, v.lcount);
   links_count<<<1, kScanBlock, 0, s>>>(v.hdr, v.lcount, v.loff);
   links_write<<<per_drop, T, 0, s>>>(v.hdr, v.adj, v.deg, v.loff, v.links, L.max_links);
